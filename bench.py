@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput benchmark of HyperANF run to stabilisation on GB300.
+
+One step = the whole hot path on one batch: initialise every counter, then
+estimate N(t) and run union passes (frontier-skipping, systolic when few
+counters change) until a pass changes nothing, then the statistics.  The
+metric is arcs x registers merged per second: every pass of Algorithm 2
+merges each arc's m registers (R runs: R*m), so a step counts
+passes * arcs * m * R; passes whose merges the frontier proves redundant are
+counted, as Algorithm 2 performs them (the gathers actually issued are
+reported beside it).
+
+Default workload: directed R-MAT scale 27 (134M nodes, edge factor 16,
+~2.1e9 arcs drawn, int64 offsets / int32 targets), m = 64 byte registers,
+one run.  Inputs (>= 10 GB of CSR and counters) are far larger than the 129 MB
+L2, so no flush is needed between steps.
+
+With torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the path needs no exchange): value = all ranks' merges / max rank time.
+``--impl reference`` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "arcs×registers merged/s per iteration"
+UNIT = "arcs*registers/s"
+
+WORKLOADS = {
+    "rmat27": dict(kind="rmat", scale=27, ef=16, sym=False, log2m=6, runs=1,
+                   text="directed R-MAT scale 27, edge factor 16 (a,b,c,d = .57,.19,.19,.05, "
+                        "scrambled labels, loops and duplicate arcs removed), m=64 byte "
+                        "registers, 1 run, frontier auto"),
+    "rmat24sym": dict(kind="rmat", scale=24, ef=16, sym=True, log2m=7, runs=1,
+                      text="symmetrised R-MAT scale 24, edge factor 16, m=128, 1 run"),
+    "web20": dict(kind="web", n=1 << 20, log2m=6, runs=8,
+                  text="web-like n=2^20 (power-law out-degree 2.1, mean 16, host blocks), "
+                       "m=64, R=8 runs batched"),
+    "er": dict(kind="er", n=10000, arcs=50000, log2m=4, runs=1,
+               text="directed ER n=10^4, 5*10^4 arcs, m=16, 1 run"),
+}
+# bounded CPU samples of the same recipes for the oracle
+CPU_SAMPLE = {"rmat27": dict(kind="rmat", scale=20, ef=16, sym=False),
+              "rmat24sym": dict(kind="rmat", scale=18, ef=16, sym=True),
+              "web20": dict(kind="web", n=1 << 16),
+              "er": dict(kind="er", n=10000, arcs=50000)}
+
+
+def make_graph(spec, seed, device):
+    from paper_1011_5599_gb300 import graphs as G
+    if spec["kind"] == "rmat":
+        return G.rmat(spec["scale"], edge_factor=spec["ef"], seed=seed, symmetrise=spec["sym"],
+                      device=device, as_numpy=False)
+    import torch
+    if spec["kind"] == "web":
+        off, tgt = G.web(spec["n"], seed=seed)
+    else:
+        off, tgt = G.er(spec["n"], spec["arcs"], seed=seed)
+    return torch.from_numpy(off).to(device), torch.from_numpy(tgt).to(device)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for(device):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and ids[device.index or 0].strip().isdigit():
+        return int(ids[device.index or 0])
+    return device.index or 0
+
+
+# ------------------------------------------------------------------ profile summary
+
+def ncu_traffic(workload):
+    """Per-launch DRAM bytes of the union kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"union_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    if not m or not h:
+        return None
+    src = open(os.path.join(ROOT, "paper_1011_5599_gb300", "csrc", "hanf_kernels.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest() != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ oracle (CPU) arm
+
+def oracle_sample(workload, seed, threads):
+    """Time the oracle (Algorithm 2, all arcs every pass) on a bounded sample
+    graph of the same recipe.  Returns (rate, seconds, description)."""
+    from oracle import oracle as O
+    from paper_1011_5599_gb300 import graphs as G
+    spec = CPU_SAMPLE[workload]
+    wl = WORKLOADS[workload]
+    if spec["kind"] == "rmat":
+        off, tgt = G.rmat(spec["scale"], edge_factor=spec["ef"], seed=seed,
+                          symmetrise=spec["sym"], device="cpu")
+        desc = (f"R-MAT scale {spec['scale']} ef {spec['ef']}{' symmetrised' if spec['sym'] else ''}"
+                f" (same recipe), {tgt.size} arcs")
+    elif spec["kind"] == "web":
+        off, tgt = G.web(spec["n"], seed=seed)
+        desc = f"web-like n={spec['n']}, {tgt.size} arcs"
+    else:
+        off, tgt = G.er(spec["n"], spec["arcs"], seed=seed)
+        desc = f"ER n={spec['n']}, {tgt.size} arcs"
+    m = 1 << wl["log2m"]
+    t0 = time.perf_counter()
+    merges = 0
+    for r in range(wl["runs"]):
+        N, T, _ = O.hyperanf(off, tgt, wl["log2m"], O.run_seed(0x5EED, r), threads=threads)
+        merges += (T + 1) * tgt.size * m
+    dt = time.perf_counter() - t0
+    return merges / dt, dt, desc + f", m={m}, R={wl['runs']}, run to stabilisation"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    threads = os.cpu_count() or 1
+    from oracle import oracle as O
+    O.build()
+    for _ in range(args.warmup):
+        oracle_sample(args.workload, 1, threads)
+    rates, secs = [], 0.0
+    desc = ""
+    for _ in range(args.steps):
+        r, s, desc = oracle_sample(args.workload, 1, threads)
+        rates.append(r)
+        secs += s
+    value = sum(rates) / len(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]["text"], "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ CUDA arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat27", choices=sorted(WORKLOADS))
+    ap.add_argument("--driver", default="host", choices=["host", "graph"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1011_5599_gb300 import build as B
+    B.build()
+    from paper_1011_5599_gb300.hanf import HyperANF
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = WORKLOADS[args.workload]
+    log2m, R = wl["log2m"], wl["runs"]
+    m = 1 << log2m
+    W = m * R
+    t_gen = time.perf_counter()
+    off, tgt = make_graph(wl, args.seed + rank, device)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    n, arcs = off.numel() - 1, tgt.numel()
+    stream = torch.cuda.current_stream(device)
+
+    h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
+                 use_graph=args.driver == "graph", profile=args.driver == "host")
+    for _ in range(args.warmup):
+        h.run()
+
+    merges = 0
+    gathered = 0
+    union_ms = 0.0
+    union_bytes = 0.0
+    launches = 0
+    passes_list, T_list = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index_for(device)) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            N, T = h.run()
+            c = h.counters()
+            merges += c["passes"] * arcs * m * R
+            gathered += c["arcs_gathered"] * m * R
+            union_ms += c["union_ms"]
+            union_bytes += (4 * c["arcs_scanned"]
+                            + W * (c["arcs_gathered"] + c["own_reads"] + c["writes"]))
+            launches += int(c["launches"])
+            passes_list.append(int(c["passes"]))
+            T_list.append(int(max(T)))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed, merges], dtype=torch.float64, device=device)
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        elapsed_all, merges_all = float(tmax.item()), float(tsum.item())
+    else:
+        elapsed_all, merges_all = elapsed, float(merges)
+    value = merges_all / elapsed_all
+    stat = {}
+    try:
+        from paper_1011_5599_gb300.hanf import stats
+        stat = stats(N[0])
+    except Exception:
+        pass
+    h.close()
+    del h
+
+    # ---- end to end through the C ABI with host buffers (pinned) ----
+    e2e = None
+    if args.e2e_steps > 0:
+        off_h = torch.empty(off.shape, dtype=torch.int64, pin_memory=True)
+        tgt_h = torch.empty(tgt.shape, dtype=torch.int32, pin_memory=True)
+        off_h.copy_(off)
+        tgt_h.copy_(tgt)
+        del off, tgt
+        torch.cuda.empty_cache()
+        e_merges, d2h = 0, 0
+        # one untimed warm-up so the workspace is in torch's cache
+        HyperANF(off_h, tgt_h, log2m, 0x5EED, runs=R, frontier="auto", device=device).close()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            with HyperANF(off_h, tgt_h, log2m, 0x5EED, runs=R, frontier="auto",
+                          device=device, use_graph=args.driver == "graph") as he:
+                Ne, Te = he.run()
+                e_merges += he.counters()["passes"] * arcs * m * R
+                d2h += sum(x.nbytes for x in Ne)
+        torch.cuda.synchronize()
+        e_el = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([e_el], dtype=torch.float64, device=device)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_el = float(tt.item())
+            mm = torch.tensor([float(e_merges)], dtype=torch.float64, device=device)
+            dist.all_reduce(mm, op=dist.ReduceOp.SUM)
+            e_merges = float(mm.item())
+        e2e = {"value": e_merges / e_el, "unit": UNIT,
+               "h2d_bytes_per_step": int((n + 1) * 8 + arcs * 4),
+               "d2h_bytes_per_step": int(d2h // args.e2e_steps),
+               "ms_per_step": 1e3 * e_el / args.e2e_steps}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, secs, desc = oracle_sample(args.workload, args.seed, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{desc}; {secs:.1f} s"}
+
+    peak, peak_kind = measured_peak()
+    steps_passes = sum(passes_list)
+    achieved = union_bytes / (union_ms / 1e3) / 1e9 if union_ms > 0 else None
+    traffic = ncu_traffic(args.workload)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_union (+ k_hub_finish)",
+            "algorithmic_bytes_per_launch": union_bytes / max(steps_passes, 1),
+            "avg_launch_ms": union_ms / max(steps_passes, 1)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed_all / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": wl["text"], "n": n, "arcs": arcs, "m": m, "runs": R,
+                       "layout": "byte", "frontier": "auto", "driver": args.driver,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "graph_gen_s": round(t_gen, 2)},
+            "T": T_list[-1], "passes_per_step": passes_list[-1],
+            "gathered_rate": gathered / elapsed if elapsed else None,
+            "stats": {k: float(v) for k, v in stat.items()},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,154 @@
+/*
+ * hanf.h -- C ABI of the GB300 HyperANF library (libhanf.so).
+ *
+ * HyperANF (Boldi, Rosa, Vigna) approximates the neighbourhood function
+ * N(t) = #{(x, y) : d(x, y) <= t} of a directed graph.  Every node keeps a
+ * HyperLogLog counter of m = 2^log2m registers (Section 3.1, Algorithm 1);
+ * node v starts with itself, and each pass replaces c[v] by the
+ * register-wise maximum of c[v] and the counters of its successors
+ * (Section 3.2, Algorithm 2).  N(t) is the sum over nodes of the counters'
+ * size() estimates.  Passes repeat until one changes no counter
+ * (stabilisation, Section 3.2); the last value printed is N(T).
+ *
+ * Conventions shared by every entry point:
+ *   - Graphs are CSR by source: offsets[n+1] (int64, offsets[0] = 0,
+ *     non-decreasing), targets[arcs] (int32, each in [0, n)).  Self-loops and
+ *     duplicate arcs are legal (max is idempotent).  n < 2^31.
+ *   - Register i of run r of node v is one byte, value 0..31 (0 = empty; the
+ *     paper's "minus infinity").  rho+ is clamped to 31.
+ *   - Hash: h(v) = splitmix64(v XOR seed_r), seed_r = splitmix64(seed + r)
+ *     unless explicit seeds are given; the register index is the top log2m
+ *     bits of h, rho+ counts the leading zeroes of the remaining bits plus one.
+ *   - size(): E = alpha_m m^2 / sum_j 2^-M[j] with the published alpha_m, and
+ *     small-range linear counting E = m ln(m/V) when E <= 5m/2 and V > 0.
+ *   - Device memory is never allocated by the library: the caller passes one
+ *     device workspace (see hanf_workspace_size) and keeps it alive until
+ *     hanf_destroy.  Streams are the caller's (cudaStream_t passed as void*).
+ *   - Every function returns HANF_OK (0) or a negative HANF_E* code and never
+ *     throws; hanf_last_error() gives a message for the calling thread.
+ */
+#ifndef HANF_H
+#define HANF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symbols of the public surface; everything else in the library is hidden. */
+#if defined(__GNUC__)
+#define HANF_API __attribute__((visibility("default")))
+#else
+#define HANF_API
+#endif
+
+#define HANF_OK 0
+#define HANF_EINVAL (-1)     /* bad argument: sizes, CSR contents, options */
+#define HANF_ENOMEM (-2)     /* workspace smaller than hanf_workspace_size  */
+#define HANF_ECUDA (-3)      /* a CUDA runtime call failed                  */
+#define HANF_ERANGE (-4)     /* history capacity exhausted before stability */
+#define HANF_ESTATE (-5)     /* call not valid in the context's state       */
+
+/* Frontier policy (Section 3.3, "tracking modified counters" and "systolic
+ * computation"). */
+#define HANF_FRONTIER_OFF 0  /* every pass merges every arc                  */
+#define HANF_FRONTIER_PULL 1 /* skip successors that did not change          */
+#define HANF_FRONTIER_AUTO 2 /* PULL, and systolic push through the transpose
+                                when fewer than n/push_den counters changed   */
+
+typedef struct hanf_ctx hanf_ctx;
+
+typedef struct hanf_opts {
+    int32_t runs;          /* R >= 1 independent seeded runs batched together  */
+    int32_t frontier;      /* HANF_FRONTIER_*; default AUTO                    */
+    int32_t push_den;      /* systolic switch below n/push_den changes; 4      */
+    int32_t small_max_deg; /* degree <= this: a lane group per node; 0 = auto  */
+    int32_t hub_min_deg;   /* degree > this: split in segments of this many
+                              arcs, a warp each; 0 = auto                      */
+    int32_t history_cap;   /* capacity of the device N(t) history; 0 = 4096    */
+    int32_t use_graph;     /* hanf_run: 1 = whole loop as one CUDA graph with a
+                              device-side while node (no host syncs)           */
+    int32_t profile;       /* 1 = time every kernel launch with CUDA events    */
+    const uint64_t *seeds; /* R explicit run seeds (host), or NULL             */
+    void *stream;          /* cudaStream_t for every launch; NULL = default    */
+} hanf_opts;
+
+/* Fill *opts with the defaults above. */
+HANF_API void hanf_default_opts(hanf_opts *opts);
+
+/* Bytes of device workspace hanf_create needs for a graph of n nodes and
+ * `arcs` arcs.  copy_graph = 1 when the CSR will be passed in host memory
+ * (the context then keeps its own device copy).  Returns HANF_EINVAL for
+ * log2m outside 4..8, n < 0 or n >= 2^31, arcs < 0, runs outside 1..8. */
+HANF_API int hanf_workspace_size(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts *opts,
+                        int32_t copy_graph, size_t *bytes_out);
+
+/* Create a context and initialise every counter (Algorithm 2: each node adds
+ * itself), leaving it at t = 0.
+ *   offsets, targets: the CSR (see conventions).  graph_on_device = 0: host
+ *     pointers, copied into the workspace (pinned host memory copies
+ *     fastest); = 1: device pointers borrowed for the context's lifetime.
+ *   workspace: device buffer of at least hanf_workspace_size() bytes, 256-byte
+ *     aligned, owned by the caller.
+ * The CSR is validated on the device (offsets monotone, targets in range);
+ * a bad graph returns HANF_EINVAL and no context.  *out is set only on
+ * success. */
+HANF_API int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
+                const int32_t *targets, int32_t graph_on_device, int32_t log2m,
+                uint64_t seed, const hanf_opts *opts, void *workspace,
+                size_t workspace_bytes);
+
+/* Algorithm 2, the sum s = sum_v size(c[v]) at the current t, for every run:
+ * N_out (host) receives R doubles.  Synchronises the stream. */
+HANF_API int hanf_estimate(hanf_ctx *ctx, double *N_out);
+
+/* One pass of Algorithm 2's main loop (t -> t+1): every counter becomes the
+ * register-wise max of itself and its successors' counters at t (Jacobi).
+ * *changed_out (host, nullable) = number of nodes whose counter changed in
+ * any run.  Synchronises the stream. */
+HANF_API int hanf_iterate(hanf_ctx *ctx, int64_t *changed_out);
+
+/* The whole of Algorithm 2: re-initialise, then print N(t) and run passes
+ * until a pass changes no counter of any run (or max_iter passes ran).
+ *   N_out (host): R x cap doubles, row r holds N_r(0..T_r) (later entries
+ *     repeat N_r(T_r) up to the global T).
+ *   T_out (host): R ints, T_r = the first pass index that changed no counter
+ *     of run r.
+ * Returns HANF_ERANGE if stabilisation needs more than cap values or
+ * max_iter passes (N_out then holds what was computed). */
+HANF_API int hanf_run(hanf_ctx *ctx, int32_t max_iter, double *N_out, int32_t cap, int32_t *T_out);
+
+/* Copy the registers of nodes [first, first+count) of run r to host memory:
+ * count * m bytes, node-major.  Synchronises the stream. */
+HANF_API int hanf_registers(hanf_ctx *ctx, int32_t run, int64_t first, int64_t count, uint8_t *out);
+
+/* Current pass index t (number of passes run since initialisation). */
+HANF_API int hanf_current_t(hanf_ctx *ctx, int32_t *t_out);
+
+/* Work and time counters since the last hanf_run / initialisation:
+ * out[0] passes, out[1] arcs scanned, out[2] arcs gathered (successor
+ * counters read), out[3] own counters read, out[4] counters written,
+ * out[5] union-kernel launches, out[6] union-kernel milliseconds (profile = 1,
+ * else 0), out[7] all kernel launches, out[8] estimator milliseconds,
+ * out[9] passes run in systolic (push) mode.  nout = entries wanted (<= 10). */
+HANF_API int hanf_counters(hanf_ctx *ctx, double *out, int32_t nout);
+
+/* Section 4 and 5 statistics of N(0..T) (host arrays, no GPU):
+ * out5 = {effective diameter at alpha, interpolated effective diameter, mean
+ * distance, variance, spid = variance / mean}, with H(t) = N(t)/max N and
+ * h(t) = H(t) - H(t-1); exclude_zero = 1 leaves out the pairs (x, x). */
+HANF_API int hanf_stats(const double *N, int32_t T, double alpha, int32_t exclude_zero, double *out5);
+
+/* Release the context (not the workspace, which belongs to the caller). */
+HANF_API void hanf_destroy(hanf_ctx *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+HANF_API const char *hanf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HANF_H */

@@ -1,0 +1,617 @@
+// C ABI of the GB300 HyperANF library: argument checking, workspace layout,
+// graph preprocessing (validation, degree classes, hub segments, transpose),
+// and the iteration drivers (host loop, or one CUDA graph whose while node
+// repeats the pass until the device-side control block says stop).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hanf.h"
+#include "hanf_internal.cuh"
+
+using hanf::DevCtl;
+using hanf::Plan;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(HANF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+constexpr int32_t kDefaultSmall = 32;
+constexpr int32_t kDefaultHub = 1024;
+constexpr int32_t kDefaultHistory = 4096;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Host-side splitmix64 output step, for the run seeds.
+uint64_t host_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// alpha_m of the HyperLogLog estimator (published constants).
+double hll_alpha(int m)
+{
+    switch (m) {
+    case 16: return 0.673;
+    case 32: return 0.697;
+    case 64: return 0.709;
+    default: return 0.7213 / (1.0 + 1.079 / (double)m);
+    }
+}
+
+struct Sizes {
+    int64_t n, arcs;
+    int32_t log2m, m, R, W;
+    int32_t d_small, d_hub, history;
+    bool copy_graph, transpose;
+    int64_t nwords, nred, ntiles, max_hub, max_seg, scan_elems;
+};
+
+struct Layout {
+    size_t off, tgt, in_off, in_src, regs0, regs1, F0, F1, cand, list0, list1, nodes;
+    size_t seg_node, seg_beg, seg_end, hub_first, hub_part, hub_any;
+    size_t blk_part, red_part, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
+    size_t seg_counts, seg_offs, totals, total;
+};
+
+int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32_t copy_graph,
+               Sizes *s)
+{
+    if (log2m < 4 || log2m > 8) return fail(HANF_EINVAL, "log2m=%d outside 4..8", log2m);
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(HANF_EINVAL, "n=%lld out of range", (long long)n);
+    if (arcs < 0) return fail(HANF_EINVAL, "arcs=%lld negative", (long long)arcs);
+    if (o.runs < 1 || o.runs > hanf::kMaxRuns)
+        return fail(HANF_EINVAL, "runs=%d outside 1..%d", o.runs, hanf::kMaxRuns);
+    if (o.frontier < HANF_FRONTIER_OFF || o.frontier > HANF_FRONTIER_AUTO)
+        return fail(HANF_EINVAL, "frontier=%d invalid", o.frontier);
+    if (o.push_den < 1) return fail(HANF_EINVAL, "push_den=%d < 1", o.push_den);
+    if (o.small_max_deg < 0 || o.hub_min_deg < 0 || o.history_cap < 0)
+        return fail(HANF_EINVAL, "negative tuning option");
+    s->n = n;
+    s->arcs = arcs;
+    s->log2m = log2m;
+    s->m = 1 << log2m;
+    s->R = o.runs;
+    s->W = s->m * s->R;
+    if (s->W != 16 && s->W != 32 && s->W != 64 && s->W != 128 && s->W != 256 && s->W != 512 &&
+        s->W != 1024 && s->W != 2048)
+        return fail(HANF_EINVAL, "runs * m = %d must be a power of two (runs 1, 2, 4 or 8)", s->W);
+    s->d_small = o.small_max_deg ? o.small_max_deg : kDefaultSmall;
+    s->d_hub = o.hub_min_deg ? o.hub_min_deg : kDefaultHub;
+    if (s->d_hub < 2) return fail(HANF_EINVAL, "hub_min_deg=%d < 2", s->d_hub);
+    if (s->d_small > s->d_hub) s->d_small = s->d_hub;
+    s->history = o.history_cap ? o.history_cap : kDefaultHistory;
+    s->copy_graph = copy_graph != 0;
+    s->transpose = o.frontier == HANF_FRONTIER_AUTO;
+    s->nwords = std::max<int64_t>(1, (n + 63) / 64);
+    s->nred = (s->nwords + hanf::kEstChunk - 1) / hanf::kEstChunk;
+    s->ntiles = hanf::classify_blocks(n);
+    s->max_hub = arcs / (s->d_hub + 1) + 1;
+    s->max_seg = 2 * (arcs / s->d_hub) + 2;
+    int64_t biggest = std::max<int64_t>({n + 1, 3 * s->ntiles + 1, s->max_hub + 1});
+    s->scan_elems = hanf::scan_tmp_elems(biggest) * 2 + 64;
+    return HANF_OK;
+}
+
+Layout make_layout(const Sizes &s)
+{
+    Layout L{};
+    size_t at = 0;
+    auto take = [&](size_t bytes) {
+        size_t here = at;
+        at += align256(std::max<size_t>(bytes, 16));
+        return here;
+    };
+    const size_t rows = (size_t)std::max<int64_t>(s.n, 1);
+    L.off = s.copy_graph ? take(sizeof(int64_t) * (s.n + 1)) : 0;
+    L.tgt = s.copy_graph ? take(sizeof(int32_t) * std::max<int64_t>(s.arcs, 1)) : 0;
+    L.in_off = s.transpose ? take(sizeof(int64_t) * (s.n + 1)) : 0;
+    L.in_src = s.transpose ? take(sizeof(int32_t) * std::max<int64_t>(s.arcs, 1)) : 0;
+    L.regs0 = take(rows * s.W);
+    L.regs1 = take(std::max(rows * s.W, sizeof(int64_t) * (s.n + 1)));
+    L.F0 = take(8 * s.nwords);
+    L.F1 = take(8 * s.nwords);
+    L.cand = take(8 * s.nwords);
+    L.list0 = take(4 * rows);
+    L.list1 = take(4 * rows);
+    L.nodes = take(4 * rows);
+    L.seg_node = take(4 * s.max_seg);
+    L.seg_beg = take(8 * s.max_seg);
+    L.seg_end = take(8 * s.max_seg);
+    L.hub_first = take(4 * (s.max_hub + 1));
+    L.hub_part = take((size_t)s.max_seg * s.W);
+    L.hub_any = take(s.max_seg);
+    L.blk_part = take(8 * s.nwords * s.R);
+    L.red_part = take(8 * s.nred * s.R);
+    L.hist = take(8 * (size_t)s.history * s.R);
+    L.lc = take(8 * (s.m + 1));
+    L.seeds = take(8 * s.R);
+    L.ctl = take(sizeof(DevCtl));
+    L.scan_tmp = take(8 * s.scan_elems);
+    L.blk_counts = take(8 * (3 * s.ntiles + 1));
+    L.blk_offs = take(8 * (3 * s.ntiles + 1));
+    L.seg_counts = take(8 * (s.max_hub + 1));
+    L.seg_offs = take(8 * (s.max_hub + 1));
+    L.totals = take(8 * 4);
+    L.total = at;
+    return L;
+}
+
+hanf_opts opts_or_default(const hanf_opts *o)
+{
+    hanf_opts d;
+    hanf_default_opts(&d);
+    return o ? *o : d;
+}
+
+}  // namespace
+
+struct hanf_ctx {
+    Plan plan;
+    Sizes sz;
+    hanf_opts opts;
+    cudaStream_t stream;
+    DevCtl host_ctl;
+    uint64_t seed;
+    int nsm;
+    cudaEvent_t ev[4];
+    double union_ms, est_ms;
+    int64_t launches;
+    cudaGraphExec_t gexec;
+    cudaStream_t capture_stream;
+    std::vector<uint64_t> seeds;
+};
+
+namespace {
+
+int read_ctl(hanf_ctx *c)
+{
+    CU(cudaMemcpyAsync(&c->host_ctl, c->plan.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return HANF_OK;
+}
+
+// Back to t = 0: control block, counters initialised (each node adds itself)
+// and N(0).
+int reset(hanf_ctx *c, int32_t max_t)
+{
+    DevCtl h;
+    std::memset(&h, 0, sizeof h);
+    h.max_t = max_t;
+    for (int r = 0; r < hanf::kMaxRuns; ++r) h.T_run[r] = -1;
+    CU(cudaMemcpyAsync(c->plan.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    CU(hanf::launch_init(c->plan, c->stream));
+    int nl = 1;
+    CU(hanf::launch_estimate(c->plan, c->stream, &nl));
+    c->launches = nl;
+    c->union_ms = 0;
+    c->est_ms = 0;
+    CU(cudaStreamSynchronize(c->stream));   // h lives on this stack frame
+    c->host_ctl = h;
+    return HANF_OK;
+}
+
+int one_pass(hanf_ctx *c)
+{
+    const bool prof = c->opts.profile != 0;
+    int nl = 0;
+    CU(hanf::launch_pass(c->plan, c->stream, 0, 0, prof ? c->ev[0] : nullptr,
+                         prof ? c->ev[1] : nullptr, &nl));
+    c->launches += nl;
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    if (prof) {
+        float ms = 0;
+        CU(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        c->union_ms += ms;
+    }
+    return HANF_OK;
+}
+
+int build_graph(hanf_ctx *c)
+{
+    if (c->gexec) return HANF_OK;
+    cudaGraph_t g = nullptr;
+    CU(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    CU(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (!c->capture_stream) CU(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+    CU(cudaStreamBeginCaptureToGraph(c->capture_stream, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    int nl = 0;
+    cudaError_t le = hanf::launch_pass(c->plan, c->capture_stream, h, 1, nullptr, nullptr, &nl);
+    cudaGraph_t captured = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->capture_stream, &captured);
+    if (le != cudaSuccess || ee != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(HANF_ECUDA, "graph capture failed: %s / %s", cudaGetErrorString(le),
+                    cudaGetErrorString(ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&c->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        c->gexec = nullptr;
+        return fail(HANF_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+    }
+    return HANF_OK;
+}
+
+int pass_launch_count(const hanf_ctx *c)
+{
+    return 4 + (c->plan.in_off ? 1 : 0) + (c->plan.n_hub ? 1 : 0) + 3;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hanf_default_opts(hanf_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->runs = 1;
+    o->frontier = HANF_FRONTIER_AUTO;
+    o->push_den = 4;
+    o->small_max_deg = 0;
+    o->hub_min_deg = 0;
+    o->history_cap = 0;
+    o->use_graph = 0;
+    o->profile = 0;
+    o->seeds = nullptr;
+    o->stream = nullptr;
+}
+
+int hanf_workspace_size(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts *opts,
+                        int32_t copy_graph, size_t *bytes_out)
+{
+    if (!bytes_out) return fail(HANF_EINVAL, "bytes_out is NULL");
+    Sizes s;
+    int rc = make_sizes(n, arcs, log2m, opts_or_default(opts), copy_graph, &s);
+    if (rc) return rc;
+    *bytes_out = make_layout(s).total;
+    return HANF_OK;
+}
+
+int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
+                const int32_t *targets, int32_t graph_on_device, int32_t log2m, uint64_t seed,
+                const hanf_opts *opts, void *workspace, size_t workspace_bytes)
+{
+    if (!out) return fail(HANF_EINVAL, "out is NULL");
+    const hanf_opts o = opts_or_default(opts);
+    Sizes s;
+    int rc = make_sizes(n, arcs, log2m, o, graph_on_device ? 0 : 1, &s);
+    if (rc) return rc;
+    if (!offsets || (arcs > 0 && !targets)) return fail(HANF_EINVAL, "CSR pointer is NULL");
+    const Layout L = make_layout(s);
+    if (!workspace) return fail(HANF_EINVAL, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return fail(HANF_EINVAL, "workspace is not 256-byte aligned");
+    if (workspace_bytes < L.total)
+        return fail(HANF_ENOMEM, "workspace of %zu bytes, %zu needed", workspace_bytes, L.total);
+
+    hanf_ctx *c = new (std::nothrow) hanf_ctx();
+    if (!c) return fail(HANF_ENOMEM, "host allocation failed");
+    auto bail = [&](int code) {
+        if (c->ev[0]) for (auto &e : c->ev) if (e) cudaEventDestroy(e);
+        delete c;
+        return code;
+    };
+    c->sz = s;
+    c->opts = o;
+    c->seed = seed;
+    c->stream = static_cast<cudaStream_t>(o.stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(fail(HANF_ECUDA, "no CUDA device"));
+    for (auto &e : c->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(HANF_ECUDA, "event create failed"));
+
+    uint8_t *ws = static_cast<uint8_t *>(workspace);
+    Plan &p = c->plan;
+    std::memset(&p, 0, sizeof p);
+    p.n = n;
+    p.arcs = arcs;
+    p.b = log2m;
+    p.m = s.m;
+    p.R = s.R;
+    p.W = s.W;
+    p.nwords = s.nwords;
+    p.nred = s.nred;
+    p.frontier = o.frontier;
+    p.push_den = o.push_den;
+    p.history_cap = s.history;
+    cudaStream_t st = c->stream;
+    if (s.copy_graph) {
+        int64_t *doff = reinterpret_cast<int64_t *>(ws + L.off);
+        int32_t *dtgt = reinterpret_cast<int32_t *>(ws + L.tgt);
+        if (cudaMemcpyAsync(doff, offsets, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st) !=
+                cudaSuccess ||
+            (arcs > 0 && cudaMemcpyAsync(dtgt, targets, sizeof(int32_t) * arcs,
+                                         cudaMemcpyHostToDevice, st) != cudaSuccess))
+            return bail(fail(HANF_ECUDA, "graph upload failed: %s",
+                             cudaGetErrorString(cudaGetLastError())));
+        p.off = doff;
+        p.tgt = dtgt;
+    } else {
+        p.off = offsets;
+        p.tgt = targets;
+    }
+    p.regs[0] = ws + L.regs0;
+    p.regs[1] = ws + L.regs1;
+    p.F[0] = reinterpret_cast<unsigned long long *>(ws + L.F0);
+    p.F[1] = reinterpret_cast<unsigned long long *>(ws + L.F1);
+    p.cand = reinterpret_cast<unsigned long long *>(ws + L.cand);
+    p.list[0] = reinterpret_cast<int32_t *>(ws + L.list0);
+    p.list[1] = reinterpret_cast<int32_t *>(ws + L.list1);
+    int32_t *nodes = reinterpret_cast<int32_t *>(ws + L.nodes);
+    p.nodes = nodes;
+    p.hub_part = ws + L.hub_part;
+    p.hub_any = ws + L.hub_any;
+    p.blk_part = reinterpret_cast<double *>(ws + L.blk_part);
+    p.red_part = reinterpret_cast<double *>(ws + L.red_part);
+    p.hist = reinterpret_cast<double *>(ws + L.hist);
+    p.lc = reinterpret_cast<const double *>(ws + L.lc);
+    p.seeds = reinterpret_cast<const uint64_t *>(ws + L.seeds);
+    p.ctl = reinterpret_cast<DevCtl *>(ws + L.ctl);
+    p.amm = hll_alpha(s.m) * (double)s.m * (double)s.m;
+    int64_t *scan_tmp = reinterpret_cast<int64_t *>(ws + L.scan_tmp);
+    int64_t *totals = reinterpret_cast<int64_t *>(ws + L.totals);
+
+    // 1. validate the CSR on the device
+    if (cudaMemsetAsync(p.ctl, 0, sizeof(DevCtl), st) != cudaSuccess ||
+        hanf::launch_validate(p, st) != cudaSuccess || read_ctl(c) != HANF_OK)
+        return bail(fail(HANF_ECUDA, "validation failed: %s", g_err.c_str()));
+    if (c->host_ctl.bad_graph)
+        return bail(fail(HANF_EINVAL, "invalid CSR: offsets must start at 0, end at arcs and "
+                                      "not decrease; targets must lie in [0, n)"));
+
+    // 2. degree classes -> [small | medium | hub] node lists
+    int64_t tot[4] = {0, 0, 0, 0};
+    if (cudaMemsetAsync(totals, 0, 4 * sizeof(int64_t), st) != cudaSuccess ||
+        hanf::launch_classify(p, s.d_small, s.d_hub, reinterpret_cast<int64_t *>(ws + L.blk_counts),
+                              reinterpret_cast<int64_t *>(ws + L.blk_offs), scan_tmp, s.scan_elems,
+                              nodes, totals, st) != cudaSuccess ||
+        cudaMemcpyAsync(tot, totals, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return bail(fail(HANF_ECUDA, "degree classification failed: %s",
+                         cudaGetErrorString(cudaGetLastError())));
+    p.n_small = tot[0];
+    p.n_med = tot[1] - tot[0];
+    p.n_hub = tot[2] - tot[1];
+
+    // 3. hub segments
+    p.seg_node = reinterpret_cast<int32_t *>(ws + L.seg_node);
+    p.seg_beg = reinterpret_cast<int64_t *>(ws + L.seg_beg);
+    p.seg_end = reinterpret_cast<int64_t *>(ws + L.seg_end);
+    p.hub_seg_first = reinterpret_cast<int32_t *>(ws + L.hub_first);
+    if (p.n_hub > 0) {
+        int64_t nseg = 0;
+        if (hanf::launch_hub_segments(p, s.d_hub, reinterpret_cast<int64_t *>(ws + L.seg_counts),
+                                      reinterpret_cast<int64_t *>(ws + L.seg_offs), scan_tmp,
+                                      s.scan_elems, const_cast<int32_t *>(p.seg_node),
+                                      const_cast<int64_t *>(p.seg_beg),
+                                      const_cast<int64_t *>(p.seg_end),
+                                      const_cast<int32_t *>(p.hub_seg_first), totals + 3,
+                                      st) != cudaSuccess ||
+            cudaMemcpyAsync(&nseg, totals + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return bail(fail(HANF_ECUDA, "hub segmentation failed: %s",
+                             cudaGetErrorString(cudaGetLastError())));
+        p.n_seg = nseg;
+    }
+
+    // 4. transpose for systolic signalling (regs[1] is free scratch until init)
+    if (s.transpose) {
+        int64_t *in_off = reinterpret_cast<int64_t *>(ws + L.in_off);
+        int32_t *in_src = reinterpret_cast<int32_t *>(ws + L.in_src);
+        if (hanf::launch_transpose(p, in_off, in_src, reinterpret_cast<int64_t *>(p.regs[1]),
+                                   scan_tmp, s.scan_elems, st) != cudaSuccess)
+            return bail(fail(HANF_ECUDA, "transpose failed: %s",
+                             cudaGetErrorString(cudaGetLastError())));
+        p.in_off = in_off;
+        p.in_src = in_src;
+    }
+
+    // 5. run seeds and the linear-counting table m ln(m/V), V = 1..m
+    c->seeds.resize(s.R);
+    for (int r = 0; r < s.R; ++r)
+        c->seeds[r] = o.seeds ? o.seeds[r] : host_splitmix64(seed + (uint64_t)r);
+    std::vector<double> lc(s.m + 1, 0.0);
+    for (int V = 1; V <= s.m; ++V) lc[V] = (double)s.m * std::log((double)s.m / (double)V);
+    if (cudaMemcpyAsync(const_cast<uint64_t *>(p.seeds), c->seeds.data(), 8 * s.R,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(const_cast<double *>(p.lc), lc.data(), 8 * (s.m + 1),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return bail(fail(HANF_ECUDA, "constant upload failed"));
+    p.union_warps = hanf::union_occupancy_warps(s.W, c->nsm);
+
+    rc = reset(c, s.history);
+    if (rc) return bail(rc);
+    *out = c;
+    return HANF_OK;
+}
+
+int hanf_estimate(hanf_ctx *c, double *N_out)
+{
+    if (!c || !N_out) return fail(HANF_EINVAL, "NULL argument");
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(N_out, c->plan.hist + (int64_t)c->host_ctl.t * c->plan.R,
+                       sizeof(double) * c->plan.R, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return HANF_OK;
+}
+
+int hanf_iterate(hanf_ctx *c, int64_t *changed_out)
+{
+    if (!c) return fail(HANF_EINVAL, "NULL context");
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    if (c->host_ctl.done) {
+        if (changed_out) *changed_out = 0;
+        return c->host_ctl.err ? fail(c->host_ctl.err, "history capacity exhausted") : HANF_OK;
+    }
+    rc = one_pass(c);
+    if (rc) return rc;
+    if (changed_out) *changed_out = (int64_t)c->host_ctl.last_changed;
+    if (c->host_ctl.err) return fail(c->host_ctl.err, "history capacity exhausted");
+    return HANF_OK;
+}
+
+int hanf_run(hanf_ctx *c, int32_t max_iter, double *N_out, int32_t cap, int32_t *T_out)
+{
+    if (!c || !N_out || !T_out) return fail(HANF_EINVAL, "NULL argument");
+    if (cap < 1 || max_iter < 1) return fail(HANF_EINVAL, "cap and max_iter must be >= 1");
+    const int32_t max_t = std::min<int32_t>(std::min(max_iter, cap), c->sz.history);
+    int rc = reset(c, max_t);
+    if (rc) return rc;
+    if (c->opts.use_graph) {
+        rc = build_graph(c);
+        if (rc) return rc;
+        CU(cudaGraphLaunch(c->gexec, c->stream));
+        rc = read_ctl(c);
+        if (rc) return rc;
+        c->launches += (int64_t)c->host_ctl.passes * pass_launch_count(c);
+    } else {
+        for (;;) {
+            rc = one_pass(c);
+            if (rc) return rc;
+            if (c->host_ctl.done) break;
+        }
+    }
+    const DevCtl &h = c->host_ctl;
+    const int32_t R = c->plan.R;
+    const int32_t T = h.t;   // N(0..T) valid (T = t at stop)
+    const int32_t have = h.err ? T : T + 1;
+    std::vector<double> hist((size_t)std::max(have, 1) * R);
+    CU(cudaMemcpyAsync(hist.data(), c->plan.hist, sizeof(double) * have * R,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (int r = 0; r < R; ++r) {
+        for (int t = 0; t < cap; ++t)
+            N_out[(int64_t)r * cap + t] = t < have ? hist[(size_t)t * R + r] : 0.0;
+        T_out[r] = h.T_run[r] >= 0 ? h.T_run[r] : T;
+    }
+    if (h.err) return fail(HANF_ERANGE, "no stabilisation within %d passes / %d values", max_iter, cap);
+    return HANF_OK;
+}
+
+int hanf_registers(hanf_ctx *c, int32_t run, int64_t first, int64_t count, uint8_t *out)
+{
+    if (!c || (!out && count > 0)) return fail(HANF_EINVAL, "NULL argument");
+    if (run < 0 || run >= c->plan.R) return fail(HANF_EINVAL, "run %d out of range", run);
+    if (first < 0 || count < 0 || first + count > c->plan.n)
+        return fail(HANF_EINVAL, "node range out of bounds");
+    if (count == 0) return HANF_OK;
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    const uint8_t *src = c->plan.regs[c->host_ctl.parity] + first * c->plan.W + (int64_t)run * c->plan.m;
+    CU(cudaMemcpy2DAsync(out, c->plan.m, src, c->plan.W, c->plan.m, count, cudaMemcpyDeviceToHost,
+                         c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return HANF_OK;
+}
+
+int hanf_current_t(hanf_ctx *c, int32_t *t_out)
+{
+    if (!c || !t_out) return fail(HANF_EINVAL, "NULL argument");
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    *t_out = c->host_ctl.t;
+    return HANF_OK;
+}
+
+int hanf_counters(hanf_ctx *c, double *out, int32_t nout)
+{
+    if (!c || !out) return fail(HANF_EINVAL, "NULL argument");
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    const DevCtl &h = c->host_ctl;
+    const double v[10] = {(double)h.passes,        (double)h.arcs_scanned, (double)h.arcs_gathered,
+                          (double)h.own_reads,     (double)h.writes,       (double)h.passes,
+                          c->union_ms,             (double)c->launches,    c->est_ms,
+                          (double)h.push_passes};
+    for (int i = 0; i < nout && i < 10; ++i) out[i] = v[i];
+    return HANF_OK;
+}
+
+int hanf_stats(const double *N, int32_t T, double alpha, int32_t exclude_zero, double *out5)
+{
+    if (!N || !out5 || T < 0) return fail(HANF_EINVAL, "bad argument");
+    const double base = exclude_zero ? N[0] : 0.0;
+    double M = N[0];
+    for (int t = 1; t <= T; ++t) M = std::max(M, N[t]);
+    double prev = 0.0, mean = 0.0, second = 0.0;
+    out5[0] = out5[1] = NAN;
+    bool found = false;
+    for (int t = 0; t <= T; ++t) {
+        const double H = (N[t] - base) / (M - base);
+        const double h = H - prev;
+        mean += t * h;
+        second += (double)t * t * h;
+        if (!found && H >= alpha) {
+            found = true;
+            out5[0] = t;
+            out5[1] = t == 0 ? 0.0 : (t - 1) + (alpha - prev) / (H - prev);
+        }
+        prev = H;
+    }
+    out5[2] = mean;
+    out5[3] = second - mean * mean;
+    out5[4] = out5[3] / mean;
+    return HANF_OK;
+}
+
+void hanf_destroy(hanf_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+const char *hanf_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,95 @@
+// Internal declarations of the GB300 HyperANF library: device-side control
+// block, the launch plan shared by every kernel, and the launchers that the
+// C ABI (hanf_api.cu) drives.  Not installed; the public surface is hanf.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hanf.h"
+
+namespace hanf {
+
+constexpr int kMaxRuns = 8;       // R <= 8 runs batched in one counter row
+constexpr int kBlock = 256;       // threads per block of the streaming kernels
+constexpr int kEstChunk = 4096;   // block partials summed by one reduction CTA
+
+// Mutable iteration state, resident in device memory so that a whole
+// HyperANF loop can run as one CUDA graph without the host looking at it.
+struct DevCtl {
+    int32_t t;           // passes completed since initialisation
+    int32_t parity;      // regs[parity] holds c_t, F[parity] the nodes changed into it
+    int32_t done;        // 1 once a pass changed no counter
+    int32_t mode;        // 0 = pull, 1 = systolic push, for the coming pass
+    int32_t max_t;       // stop (with err = HANF_ERANGE) after this many passes
+    int32_t err;         // HANF_OK or HANF_ERANGE
+    int32_t bad_graph;   // set by the CSR validator
+    int32_t pad_;
+    int32_t T_run[kMaxRuns];                 // first pass that left run r unchanged
+    unsigned long long list_count[2];        // length of changed-node list [parity]
+    unsigned long long run_changed[kMaxRuns];
+    unsigned long long last_changed;         // nodes changed by the last pass
+    // work counters since initialisation
+    unsigned long long passes, push_passes, arcs_scanned, arcs_gathered, own_reads, writes;
+};
+
+// Everything a kernel needs that does not change between passes.  Passed by
+// value, so a captured graph replays it unchanged.
+struct Plan {
+    int64_t n, arcs;
+    int32_t b, m, R, W;               // W = R * m bytes per node row
+    int64_t nwords;                   // 64-node blocks = bitmap words
+    int64_t nred;                     // first-level reduction CTAs per run
+    const int64_t *off;
+    const int32_t *tgt;
+    const int64_t *in_off;            // transpose (systolic mode), or null
+    const int32_t *in_src;
+    uint8_t *regs[2];                 // ping-pong counter arrays, n x W bytes
+    unsigned long long *F[2];         // changed-node bitmaps (parity-indexed)
+    unsigned long long *cand;         // systolic candidates of the coming pass
+    int32_t *list[2];                 // changed-node lists (parity-indexed)
+    const int32_t *nodes;             // [small | medium | hub] node lists
+    int64_t n_small, n_med, n_hub;
+    const int32_t *seg_node;          // hub segments: node, arc range
+    const int64_t *seg_beg;
+    const int64_t *seg_end;
+    int64_t n_seg;
+    const int32_t *hub_seg_first;     // n_hub + 1 segment offsets
+    uint8_t *hub_part;                // n_seg x W partial maxima
+    uint8_t *hub_any;                 // n_seg flags: segment merged something
+    double *blk_part;                 // R x nwords estimator partials
+    double *red_part;                 // R x nred
+    double *hist;                     // history_cap x R values of N(t)
+    const double *lc;                 // m+1 linear-counting values m ln(m/V)
+    double amm;                       // alpha_m m^2
+    const uint64_t *seeds;            // R run seeds
+    int32_t frontier, push_den;
+    int32_t history_cap;
+    int32_t union_warps;              // resident warps of the union launch
+    DevCtl *ctl;
+};
+
+// ---- launchers (hanf_kernels.cu); all asynchronous on `s` ----
+cudaError_t launch_validate(const Plan &p, cudaStream_t s);
+cudaError_t launch_init(const Plan &p, cudaStream_t s);
+cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch);
+cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
+                        cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch);
+int union_occupancy_warps(int W, int nsm);
+
+// Preprocessing (create time).
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *tmp,
+                               int64_t tmp_elems, cudaStream_t s);
+int64_t scan_tmp_elems(int64_t count);
+cudaError_t launch_classify(const Plan &p, int32_t d_small, int32_t d_hub, int64_t *blk_counts,
+                            int64_t *blk_offs, int64_t *tmp, int64_t tmp_elems, int32_t *nodes,
+                            int64_t *totals_dev, cudaStream_t s);
+cudaError_t launch_hub_segments(const Plan &p, int32_t d_hub, int64_t *seg_counts,
+                                int64_t *seg_offs, int64_t *tmp, int64_t tmp_elems,
+                                int32_t *seg_node, int64_t *seg_beg, int64_t *seg_end,
+                                int32_t *hub_seg_first, int64_t *total_dev, cudaStream_t s);
+cudaError_t launch_transpose(const Plan &p, int64_t *in_off, int32_t *in_src, int64_t *cursor,
+                             int64_t *tmp, int64_t tmp_elems, cudaStream_t s);
+int64_t classify_blocks(int64_t n);
+
+}  // namespace hanf

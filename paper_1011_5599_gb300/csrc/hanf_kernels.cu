@@ -1,0 +1,933 @@
+// CUDA kernels of the GB300 HyperANF library (sm_103a).
+//
+// Counter layout: node v owns one row of W = R*m bytes at regs[p] + v*W; run
+// r's m registers are bytes [r*m, (r+1)*m) of the row, one register per byte
+// (values 0..31).  A row is moved as W/16 uint4 vectors by a "lane group" of
+// LANES = min(32, W/16) threads, VPL = W/(16*LANES) vectors per lane, so every
+// gather of a successor counter is a run of fully used 16-byte loads.
+//
+// The union (Algorithm 2's inner loop, Section 3.2) is Jacobi: pass t reads
+// regs[p] (= c_t) and writes regs[p^1].  regs[p^1] holds c_{t-1} on entry, so
+// a node needs a store only if its counter changes now or changed in the
+// previous pass; every other row already equals c_{t+1}.  Successors that did
+// not change in the previous pass are skipped (Section 3.3, tracking modified
+// counters): the changed set is a bitmap F[p] of n bits.
+#include <cuda_runtime.h>
+
+#include "hanf_internal.cuh"
+
+namespace hanf {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- hashing
+
+// splitmix64 output step (Steele, Lea, Flood): golden-ratio increment, then
+// two xor-shift-multiply rounds and a final xor-shift.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- rows
+
+template <int LANES, int VPL>
+struct Row {
+    uint4 v[VPL];
+};
+
+__device__ __forceinline__ uint4 vmax4(uint4 a, uint4 b)
+{
+    return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z),
+                      __vmaxu4(a.w, b.w));
+}
+
+__device__ __forceinline__ bool veq(uint4 a, uint4 b)
+{
+    return ((a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w)) == 0u;
+}
+
+template <int LANES, int VPL>
+__device__ __forceinline__ void row_zero(Row<LANES, VPL> &r)
+{
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) r.v[k] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+template <int LANES, int VPL>
+__device__ __forceinline__ void row_load(Row<LANES, VPL> &r, const uint8_t *base, int64_t row,
+                                         int gl)
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(base) + row * (LANES * VPL) + gl;
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) r.v[k] = __ldg(q + k * LANES);
+}
+
+template <int LANES, int VPL>
+__device__ __forceinline__ void row_store(uint8_t *base, int64_t row, const Row<LANES, VPL> &r,
+                                          int gl)
+{
+    uint4 *q = reinterpret_cast<uint4 *>(base) + row * (LANES * VPL) + gl;
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) q[k * LANES] = r.v[k];
+}
+
+template <int LANES, int VPL>
+__device__ __forceinline__ void row_max(Row<LANES, VPL> &a, const Row<LANES, VPL> &b)
+{
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) a.v[k] = vmax4(a.v[k], b.v[k]);
+}
+
+// Register-wise max across the lane groups of a warp (all lanes take part).
+template <int LANES, int VPL>
+__device__ __forceinline__ void row_warp_max(Row<LANES, VPL> &r)
+{
+#pragma unroll
+    for (int s = LANES; s < 32; s <<= 1) {
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) {
+            r.v[k].x = __vmaxu4(r.v[k].x, __shfl_xor_sync(kFull, r.v[k].x, s));
+            r.v[k].y = __vmaxu4(r.v[k].y, __shfl_xor_sync(kFull, r.v[k].y, s));
+            r.v[k].z = __vmaxu4(r.v[k].z, __shfl_xor_sync(kFull, r.v[k].z, s));
+            r.v[k].w = __vmaxu4(r.v[k].w, __shfl_xor_sync(kFull, r.v[k].w, s));
+        }
+    }
+}
+
+template <int LANES>
+__device__ __forceinline__ uint32_t group_or(uint32_t x)
+{
+#pragma unroll
+    for (int s = 1; s < LANES; s <<= 1) x |= __shfl_xor_sync(kFull, x, s);
+    return x;
+}
+
+__device__ __forceinline__ bool test_bit(const unsigned long long *bits, int32_t v)
+{
+    return (__ldg(bits + (v >> 6)) >> (v & 63)) & 1ull;
+}
+
+// ---------------------------------------------------------------- union
+
+// Merge the counters of arcs e, e+stride, ... < end into acc (skipping
+// successors outside the changed set unless all_succ).  U arcs are in flight
+// per step so that each lane group keeps several gathers outstanding.
+template <int LANES, int VPL, int U>
+__device__ __forceinline__ void gather(const int32_t *__restrict__ tgt, const uint8_t *rc,
+                                       const unsigned long long *Fc, bool all_succ, int64_t e,
+                                       int64_t end, int64_t stride, int gl,
+                                       Row<LANES, VPL> &acc, bool &any, uint32_t &gathered)
+{
+    for (; e < end; e += U * stride) {
+        int32_t w[U];
+        bool tk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t eu = e + u * stride;
+            w[u] = eu < end ? __ldg(tgt + eu) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) tk[u] = w[u] >= 0 && (all_succ || test_bit(Fc, w[u]));
+        Row<LANES, VPL> x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (tk[u]) row_load(x[u], rc, w[u], gl);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (tk[u]) {
+                row_max(acc, x[u]);
+                any = true;
+                ++gathered;
+            }
+    }
+}
+
+// New counter of v = max(acc, c_t[v]); store it if it changed or if v changed
+// in the previous pass (its row in the target buffer is then stale).  Returns
+// the mask of runs whose counter changed (same value on all lanes of the
+// group).  Every lane of the warp must call it.
+template <int LANES, int VPL>
+__device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Row<LANES, VPL> &acc,
+                                                bool need, bool inR, int32_t v, int gl,
+                                                uint32_t &c_own, uint32_t &c_write)
+{
+    Row<LANES, VPL> own, nw;
+    uint32_t mask = 0;
+    if (need) {
+        row_load(own, p.regs[cur], v, gl);
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) {
+            nw.v[k] = vmax4(acc.v[k], own.v[k]);
+            const int run = ((k * LANES + gl) << 4) >> p.b;
+            if (!veq(nw.v[k], own.v[k])) mask |= 1u << run;
+        }
+    }
+    mask = group_or<LANES>(mask);
+    if (need && (mask || inR)) {
+        row_store(p.regs[cur ^ 1], v, nw, gl);
+        if (gl == 0) ++c_write;
+    }
+    if (need && gl == 0) ++c_own;
+    return mask;
+}
+
+// Record the nodes whose counters changed: bitmap bit, compact list entry and
+// per-run counts.  Called by all lanes; `leader` marks one lane per node.
+__device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, int32_t v,
+                                          uint32_t mask)
+{
+    const bool ch = leader && mask != 0;
+    const unsigned bal = __ballot_sync(kFull, ch);
+    if (bal == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int first = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if (lane == first)
+        base = atomicAdd(&p.ctl->list_count[cur ^ 1], (unsigned long long)__popc(bal));
+    base = __shfl_sync(kFull, base, first);
+    if (ch) {
+        const int rank = __popc(bal & ((1u << lane) - 1u));
+        p.list[cur ^ 1][base + rank] = v;
+        atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
+    }
+    for (int r = 0; r < p.R; ++r) {
+        const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u));
+        if (lane == 0 && br) atomicAdd(&p.ctl->run_changed[r], (unsigned long long)__popc(br));
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
+{
+#pragma unroll
+    for (int s = 16; s; s >>= 1) x += __shfl_xor_sync(kFull, x, s);
+    return x;
+}
+
+// One union pass.  Work items, handed to warps round-robin: hub segments
+// (a warp merges up to hub_min_deg arcs into a partial row), then medium
+// nodes (a warp per node, lane groups striding over the arcs), then small
+// nodes (a lane group per node, GPW nodes per warp).
+template <int LANES, int VPL>
+__global__ void __launch_bounds__(kBlock) k_union(Plan p)
+{
+    constexpr int GPW = 32 / LANES;
+    constexpr int U = VPL >= 4 ? 2 : 4;
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const bool all_succ = first || p.frontier == HANF_FRONTIER_OFF;
+    const bool push = ctl->mode == 1;
+    const uint8_t *rc = p.regs[cur];
+    const unsigned long long *Fc = p.F[cur];
+    const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t n_small_items = (p.n_small + GPW - 1) / GPW;
+    const int64_t med_end = p.n_seg + p.n_med;
+    const int64_t total = med_end + n_small_items;
+    uint32_t c_gather = 0, c_own = 0, c_write = 0;
+    unsigned long long c_scan = 0;
+
+    for (int64_t it = warp; it < total; it += nwarps) {
+        Row<LANES, VPL> acc;
+        row_zero(acc);
+        bool any = false;
+        if (it < p.n_seg) {
+            const int32_t v = p.seg_node[it];
+            const bool take = !push || test_bit(p.cand, v);
+            if (take) {
+                const int64_t beg = p.seg_beg[it], end = p.seg_end[it];
+                gather<LANES, VPL, U>(p.tgt, rc, Fc, all_succ, beg + g, end, GPW, gl, acc, any,
+                                      c_gather);
+                if (lane == 0) c_scan += end - beg;
+            }
+            row_warp_max(acc);
+            any = __any_sync(kFull, any);
+            if (g == 0) row_store(p.hub_part, it, acc, gl);
+            if (lane == 0) p.hub_any[it] = any ? 1 : 0;
+        } else if (it < med_end) {
+            const int32_t v = p.nodes[p.n_small + (it - p.n_seg)];
+            const bool take = !push || test_bit(p.cand, v);
+            if (take) {
+                const int64_t beg = __ldg(p.off + v), end = __ldg(p.off + v + 1);
+                gather<LANES, VPL, U>(p.tgt, rc, Fc, all_succ, beg + g, end, GPW, gl, acc, any,
+                                      c_gather);
+                if (lane == 0) c_scan += end - beg;
+            }
+            row_warp_max(acc);
+            any = __any_sync(kFull, any);
+            const bool inR = take && !first && test_bit(Fc, v);
+            const bool need = take && (any || inR) && g == 0;
+            const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+            warp_mark(p, cur, lane == 0, v, mask);
+        } else {
+            const int64_t idx = (it - med_end) * GPW + g;
+            const bool valid = idx < p.n_small;
+            const int32_t v = valid ? p.nodes[idx] : 0;
+            const bool take = valid && (!push || test_bit(p.cand, v));
+            if (take) {
+                const int64_t beg = __ldg(p.off + v), end = __ldg(p.off + v + 1);
+                gather<LANES, VPL, U>(p.tgt, rc, Fc, all_succ, beg, end, 1, gl, acc, any,
+                                      c_gather);
+                if (gl == 0) c_scan += end - beg;
+            }
+            const bool inR = take && !first && test_bit(Fc, v);
+            const bool need = take && (any || inR);
+            const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+            warp_mark(p, cur, gl == 0 && valid, v, mask);
+        }
+    }
+    // work counters: one atomic per warp and counter
+    const unsigned long long s_scan = warp_sum_u64(c_scan);
+    const unsigned long long s_gather = warp_sum_u64(gl == 0 ? c_gather : 0u);
+    const unsigned long long s_own = warp_sum_u64(c_own);
+    const unsigned long long s_write = warp_sum_u64(c_write);
+    if (lane == 0) {
+        DevCtl *c = p.ctl;
+        if (s_scan) atomicAdd(&c->arcs_scanned, s_scan);
+        if (s_gather) atomicAdd(&c->arcs_gathered, s_gather);
+        if (s_own) atomicAdd(&c->own_reads, s_own);
+        if (s_write) atomicAdd(&c->writes, s_write);
+    }
+}
+
+// Hub nodes: combine the segment partials written by k_union, then finish
+// like any other node.  A lane group per hub.
+template <int LANES, int VPL>
+__global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
+{
+    constexpr int GPW = 32 / LANES;
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done || p.n_hub == 0) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const bool push = ctl->mode == 1;
+    const unsigned long long *Fc = p.F[cur];
+    const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_own = 0, c_write = 0;
+    for (int64_t base = warp * GPW; base < p.n_hub; base += nwarps * GPW) {
+        const int64_t h = base + g;
+        const bool valid = h < p.n_hub;
+        const int32_t v = valid ? p.nodes[p.n_small + p.n_med + h] : 0;
+        const bool take = valid && (!push || test_bit(p.cand, v));
+        Row<LANES, VPL> acc;
+        row_zero(acc);
+        bool any = false;
+        if (take) {
+            for (int32_t s = p.hub_seg_first[h]; s < p.hub_seg_first[h + 1]; ++s) {
+                if (p.hub_any[s]) {
+                    Row<LANES, VPL> x;
+                    row_load(x, p.hub_part, s, gl);
+                    row_max(acc, x);
+                    any = true;
+                }
+            }
+        }
+        const bool inR = take && !first && test_bit(Fc, v);
+        const bool need = take && (any || inR);
+        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+        warp_mark(p, cur, gl == 0 && valid, v, mask);
+    }
+    const unsigned long long s_own = warp_sum_u64(c_own);
+    const unsigned long long s_write = warp_sum_u64(c_write);
+    if (lane == 0) {
+        if (s_own) atomicAdd(&p.ctl->own_reads, s_own);
+        if (s_write) atomicAdd(&p.ctl->writes, s_write);
+    }
+}
+
+// ---------------------------------------------------------------- pass control
+
+// Choose pull or systolic push for the coming pass and reset its counters.
+// Section 3.3: systolic computation once fewer than n/push_den counters
+// changed.
+__global__ void k_prep(Plan p)
+{
+    DevCtl *c = p.ctl;
+    if (c->done) return;
+    const int push = p.frontier == HANF_FRONTIER_AUTO && p.in_off != nullptr && c->t > 0 &&
+                     (long long)c->last_changed * p.push_den < p.n;
+    c->mode = push;
+    c->list_count[c->parity ^ 1] = 0;
+    for (int r = 0; r < kMaxRuns; ++r) c->run_changed[r] = 0;
+}
+
+__global__ void k_clear(Plan p)
+{
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    unsigned long long *fn = p.F[c->parity ^ 1];
+    const bool push = c->mode == 1;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.nwords;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        fn[i] = 0ull;
+        if (push) p.cand[i] = 0ull;
+    }
+}
+
+// Systolic signalling: every node changed by the previous pass marks itself
+// and its predecessors (through the transposed graph) as candidates.
+__global__ void k_mark(Plan p)
+{
+    const DevCtl *c = p.ctl;
+    if (c->done || c->mode != 1) return;
+    const int cur = c->parity;
+    const int64_t cnt = (int64_t)c->list_count[cur];
+    const int32_t *lst = p.list[cur];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < cnt; i += nwarps) {
+        const int32_t w = lst[i];
+        if (lane == 0) atomicOr(&p.cand[w >> 6], 1ull << (w & 63));
+        const int64_t beg = p.in_off[w], end = p.in_off[w + 1];
+        for (int64_t e = beg + lane; e < end; e += 32) {
+            const int32_t u = __ldg(p.in_src + e);
+            atomicOr(&p.cand[u >> 6], 1ull << (u & 63));
+        }
+    }
+}
+
+// End of a pass: stop if nothing changed (T = t), otherwise advance t and
+// swap the buffers.  In graph mode it also sets the while-node condition.
+__global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
+{
+    DevCtl *c = p.ctl;
+    unsigned keep = 0;
+    if (!c->done) {
+        const int nxt = c->parity ^ 1;
+        const unsigned long long changed = c->list_count[nxt];
+        c->last_changed = changed;
+        c->passes += 1;
+        if (c->mode == 1) c->push_passes += 1;
+        for (int r = 0; r < p.R; ++r)
+            if (c->T_run[r] < 0 && c->run_changed[r] == 0) c->T_run[r] = c->t;
+        if (changed == 0) {
+            c->done = 1;
+        } else {
+            c->t += 1;
+            c->parity = nxt;
+            if (c->t >= c->max_t || c->t >= p.history_cap) {
+                c->err = HANF_ERANGE;
+                c->done = 1;
+            } else {
+                keep = 1;
+            }
+        }
+    }
+    if (use_cond) cudaGraphSetConditional(h, keep);
+}
+
+// ---------------------------------------------------------------- estimator
+
+// size() of run r of node v (Algorithm 1 with linear counting).  The sum of
+// 2^-M[j] is exact: it is accumulated as the integer sum of 2^(31-M[j]).
+__device__ __forceinline__ double node_size(const Plan &p, const uint8_t *rc, int64_t v, int r)
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(rc + v * p.W + (int64_t)r * p.m);
+    unsigned long long S = 0;
+    int V = 0;
+    for (int k = 0; k < (p.m >> 4); ++k) {
+        const uint4 x = q[k];
+        const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int s = 0; s < 32; s += 8) {
+                const uint32_t M = (w4[j] >> s) & 0xffu;
+                S += 1ull << (31 - M);
+                V += M == 0;
+            }
+        }
+    }
+    const double sum = (double)S * 0x1p-31;
+    const double Z = 1.0 / sum;
+    double E = p.amm * Z;
+    if (E <= 2.5 * (double)p.m && V > 0) E = p.lc[V];
+    return E;
+}
+
+// Per 64-node block and run: sum of size() over the block, recomputed only
+// for blocks with a counter changed by the last pass (Section 3.3, harmonic
+// partial sums of small blocks).  A warp per (run, block); the warp sum uses
+// a fixed butterfly, so the partial is a deterministic function of the
+// block's registers.
+__global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
+{
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    const bool all = c->t == 0;
+    const uint8_t *rc = p.regs[c->parity];
+    const unsigned long long *Fc = p.F[c->parity];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t items = p.nwords * p.R;
+    for (int64_t it = warp; it < items; it += nwarps) {
+        const int r = (int)(it / p.nwords);
+        const int64_t blk = it - (int64_t)r * p.nwords;
+        if (!all && Fc[blk] == 0ull) continue;
+        const int64_t v0 = blk * 64 + lane, v1 = v0 + 32;
+        const double e0 = v0 < p.n ? node_size(p, rc, v0, r) : 0.0;
+        const double e1 = v1 < p.n ? node_size(p, rc, v1, r) : 0.0;
+        double s = e0 + e1;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane == 0) p.blk_part[it] = s;
+    }
+}
+
+// Fixed-shape tree over the block partials: first level, one CTA per run and
+// kEstChunk consecutive blocks.
+__global__ void __launch_bounds__(kBlock) k_est_reduce1(Plan p)
+{
+    __shared__ double sh[kBlock];
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    const int r = blockIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * kEstChunk;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < kEstChunk; j += kBlock) {
+        const int64_t i = i0 + j;
+        if (i < p.nwords) s += p.blk_part[(int64_t)r * p.nwords + i];
+    }
+    sh[threadIdx.x] = s;
+    for (int w = kBlock / 2; w; w >>= 1) {
+        __syncthreads();
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    }
+    if (threadIdx.x == 0) p.red_part[(int64_t)r * p.nred + blockIdx.x] = sh[0];
+}
+
+// Second level: N(t) of run r into the history.
+__global__ void __launch_bounds__(kBlock) k_est_reduce2(Plan p)
+{
+    __shared__ double sh[kBlock];
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    const int r = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < p.nred; i += kBlock) s += p.red_part[(int64_t)r * p.nred + i];
+    sh[threadIdx.x] = s;
+    for (int w = kBlock / 2; w; w >>= 1) {
+        __syncthreads();
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    }
+    if (threadIdx.x == 0) p.hist[(int64_t)c->t * p.R + r] = sh[0];
+}
+
+// ---------------------------------------------------------------- init
+
+// Algorithm 2's initialisation: every counter empty, then node v adds itself
+// (Algorithm 1's add): register h_b(v) <- min(rho+(h^b(v)), 31) with
+// h = splitmix64(v XOR seed_r).  One thread per 16-byte chunk of the counter
+// array; both ping-pong buffers get c_0.
+__global__ void __launch_bounds__(kBlock) k_init(Plan p)
+{
+    const int64_t cpr = p.W >> 4;
+    const int64_t total = p.n * cpr;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = c / cpr;
+        const int byte0 = (int)(c - v * cpr) << 4;
+        const int r = byte0 >> p.b;
+        const int o = byte0 & (p.m - 1);
+        const uint64_t h = splitmix64((uint64_t)v ^ p.seeds[r]);
+        const int idx = (int)(h >> (64 - p.b));
+        const uint64_t rest = h << p.b;
+        int rho = rest ? __clzll((long long)rest) + 1 : 64 - p.b + 1;
+        rho = rho > 31 ? 31 : rho;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        const int rel = idx - o;
+        if (rel >= 0 && rel < 16) w[rel >> 2] = (uint32_t)rho << ((rel & 3) * 8);
+        const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4 *>(p.regs[0])[c] = val;
+        reinterpret_cast<uint4 *>(p.regs[1])[c] = val;
+    }
+}
+
+// CSR validation: offsets start at 0, end at arcs and never decrease; every
+// target lies in [0, n).
+__global__ void k_validate(Plan p)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool bad = false;
+    for (int64_t i = i0; i <= p.n; i += stride) {
+        const int64_t o = p.off[i];
+        if (i == 0 && o != 0) bad = true;
+        if (i == p.n && o != p.arcs) bad = true;
+        if (i < p.n && p.off[i + 1] < o) bad = true;
+    }
+    for (int64_t e = i0; e < p.arcs; e += stride) {
+        const int32_t w = p.tgt[e];
+        if (w < 0 || (int64_t)w >= p.n) bad = true;
+    }
+    if (bad) p.ctl->bad_graph = 1;
+}
+
+// ---------------------------------------------------------------- scans
+
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kBlock * kScanItems;
+
+// Exclusive scan of one value per thread across the block; *total gets the sum.
+__device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t *total)
+{
+    __shared__ int64_t warp_tot[kBlock / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = x;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const int64_t y = __shfl_up_sync(kFull, inc, s);
+        if (lane >= s) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    int64_t off = 0, tot = 0;
+    for (int w = 0; w < kBlock / 32; ++w) {
+        if (w < wid) off += warp_tot[w];
+        tot += warp_tot[w];
+    }
+    if (total) *total = tot;
+    return off + inc - x;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_tile_sums(const int64_t *in, int64_t count,
+                                                           int64_t *sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < count) s += in[base + k];
+    int64_t tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_tile_apply(const int64_t *in, int64_t *out,
+                                                            int64_t count,
+                                                            const int64_t *tile_offs)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < count ? in[base + k] : 0;
+        s += v[k];
+    }
+    int64_t run = block_excl_scan(s, nullptr) + (tile_offs ? tile_offs[blockIdx.x] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < count) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+// ---------------------------------------------------------------- preprocessing
+
+constexpr int kClassPerThread = 4;
+constexpr int kClassTile = kBlock * kClassPerThread;
+
+__device__ __forceinline__ int node_class(int64_t deg, int32_t d_small, int32_t d_hub)
+{
+    return deg == 0 ? -1 : (deg <= d_small ? 0 : (deg <= d_hub ? 1 : 2));
+}
+
+// Per tile of nodes, how many fall in each class (small, medium, hub);
+// counts[c * ntiles + tile].
+__global__ void __launch_bounds__(kBlock) k_class_count(Plan p, int32_t d_small, int32_t d_hub,
+                                                        int64_t *counts, int64_t ntiles)
+{
+    int64_t c3[3] = {0, 0, 0};
+    const int64_t v0 = (int64_t)blockIdx.x * kClassTile + (int64_t)threadIdx.x * kClassPerThread;
+    for (int k = 0; k < kClassPerThread; ++k) {
+        const int64_t v = v0 + k;
+        if (v < p.n) {
+            const int c = node_class(p.off[v + 1] - p.off[v], d_small, d_hub);
+            if (c >= 0) c3[c] += 1;
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        int64_t tot;
+        block_excl_scan(c3[c], &tot);
+        if (threadIdx.x == 0) counts[c * ntiles + blockIdx.x] = tot;
+    }
+}
+
+// Scatter node ids into [small | medium | hub] in node order.
+__global__ void __launch_bounds__(kBlock) k_class_scatter(Plan p, int32_t d_small, int32_t d_hub,
+                                                          const int64_t *offs, int64_t ntiles,
+                                                          int32_t *nodes)
+{
+    int cls[kClassPerThread];
+    int64_t c3[3] = {0, 0, 0};
+    const int64_t v0 = (int64_t)blockIdx.x * kClassTile + (int64_t)threadIdx.x * kClassPerThread;
+    for (int k = 0; k < kClassPerThread; ++k) {
+        const int64_t v = v0 + k;
+        cls[k] = v < p.n ? node_class(p.off[v + 1] - p.off[v], d_small, d_hub) : -1;
+        if (cls[k] >= 0) c3[cls[k]] += 1;
+    }
+    int64_t pos[3];
+    for (int c = 0; c < 3; ++c) pos[c] = block_excl_scan(c3[c], nullptr) + offs[c * ntiles + blockIdx.x];
+    for (int k = 0; k < kClassPerThread; ++k)
+        if (cls[k] >= 0) nodes[pos[cls[k]]++] = (int32_t)(v0 + k);
+}
+
+__global__ void k_hub_seg_count(Plan p, int32_t d_hub, const int32_t *hubs, int64_t n_hub,
+                                int64_t *seg_counts)
+{
+    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h <= n_hub;
+         h += (int64_t)gridDim.x * blockDim.x) {
+        if (h == n_hub) {
+            seg_counts[h] = 0;
+        } else {
+            const int32_t v = hubs[h];
+            const int64_t deg = p.off[v + 1] - p.off[v];
+            seg_counts[h] = (deg + d_hub - 1) / d_hub;
+        }
+    }
+}
+
+__global__ void k_hub_seg_fill(Plan p, int32_t d_hub, const int32_t *hubs, int64_t n_hub,
+                               const int64_t *seg_offs, int32_t *seg_node, int64_t *seg_beg,
+                               int64_t *seg_end, int32_t *hub_seg_first)
+{
+    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h <= n_hub;
+         h += (int64_t)gridDim.x * blockDim.x) {
+        hub_seg_first[h] = (int32_t)seg_offs[h];
+        if (h == n_hub) continue;
+        const int32_t v = hubs[h];
+        const int64_t b = p.off[v], e = p.off[v + 1];
+        int64_t s = seg_offs[h];
+        for (int64_t a = b; a < e; a += d_hub, ++s) {
+            seg_node[s] = v;
+            seg_beg[s] = a;
+            seg_end[s] = a + d_hub < e ? a + d_hub : e;
+        }
+    }
+}
+
+__global__ void k_in_degree(Plan p, unsigned long long *cnt)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < p.arcs;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[p.tgt[e]], 1ull);
+}
+
+__global__ void k_transpose_fill(Plan p, const int64_t *in_off, unsigned long long *cursor,
+                                 int32_t *in_src)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < p.n; v += nwarps) {
+        for (int64_t e = p.off[v] + lane; e < p.off[v + 1]; e += 32) {
+            const int32_t w = p.tgt[e];
+            const unsigned long long k = atomicAdd(&cursor[w], 1ull);
+            in_src[in_off[w] + (int64_t)k] = (int32_t)v;
+        }
+    }
+}
+
+int grid_for(int64_t work, int per_block, int64_t cap = 152 * 32)
+{
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------- dispatch on row width
+
+template <int LANES, int VPL>
+struct UnionKernels {
+    static cudaError_t launch(const Plan &p, cudaStream_t s)
+    {
+        const int blocks = (p.union_warps * 32 + kBlock - 1) / kBlock;
+        k_union<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    static cudaError_t launch_hub(const Plan &p, cudaStream_t s)
+    {
+        constexpr int GPW = 32 / LANES;
+        const int blocks = grid_for((p.n_hub + GPW - 1) / GPW, kBlock / 32, 152 * 16);
+        k_hub_finish<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+        return cudaGetLastError();
+    }
+    static int occupancy()
+    {
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_union<LANES, VPL>, kBlock, 0);
+        return nb;
+    }
+};
+
+template <typename F>
+cudaError_t with_width(int W, F &&f)
+{
+    switch (W) {
+    case 16: return f(UnionKernels<1, 1>());
+    case 32: return f(UnionKernels<2, 1>());
+    case 64: return f(UnionKernels<4, 1>());
+    case 128: return f(UnionKernels<8, 1>());
+    case 256: return f(UnionKernels<16, 1>());
+    case 512: return f(UnionKernels<32, 1>());
+    case 1024: return f(UnionKernels<32, 2>());
+    case 2048: return f(UnionKernels<32, 4>());
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+
+int union_occupancy_warps(int W, int nsm)
+{
+    int nb = 0;
+    with_width(W, [&](auto k) {
+        nb = decltype(k)::occupancy();
+        return cudaSuccess;
+    });
+    if (nb < 1) nb = 1;
+    return nb * nsm * (kBlock / 32);
+}
+
+cudaError_t launch_validate(const Plan &p, cudaStream_t s)
+{
+    k_validate<<<grid_for(p.arcs > p.n ? p.arcs : p.n + 1, kBlock, 152 * 64), kBlock, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Plan &p, cudaStream_t s)
+{
+    k_init<<<grid_for(p.n * (p.W >> 4), kBlock, 152 * 64), kBlock, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
+{
+    k_est_blocks<<<grid_for(p.nwords * p.R, kBlock / 32, 152 * 64), kBlock, 0, s>>>(p);
+    k_est_reduce1<<<dim3((unsigned)p.nred, (unsigned)p.R), kBlock, 0, s>>>(p);
+    k_est_reduce2<<<p.R, kBlock, 0, s>>>(p);
+    if (nlaunch) *nlaunch += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
+                        cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch)
+{
+    k_prep<<<1, 1, 0, s>>>(p);
+    k_clear<<<grid_for(p.nwords, kBlock, 152 * 16), kBlock, 0, s>>>(p);
+    if (p.in_off) k_mark<<<152 * 8, kBlock, 0, s>>>(p);
+    if (ev0) cudaEventRecord(ev0, s);
+    cudaError_t err = with_width(p.W, [&](auto k) { return decltype(k)::launch(p, s); });
+    if (err != cudaSuccess) return err;
+    if (p.n_hub) {
+        err = with_width(p.W, [&](auto k) { return decltype(k)::launch_hub(p, s); });
+        if (err != cudaSuccess) return err;
+    }
+    if (ev1) cudaEventRecord(ev1, s);
+    k_post<<<1, 1, 0, s>>>(p, h, use_cond);
+    if (nlaunch) *nlaunch += 4 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    return launch_estimate(p, s, nlaunch);
+}
+
+int64_t scan_tmp_elems(int64_t count)
+{
+    int64_t total = 0;
+    while (count > kScanTile) {
+        const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+        total += 2 * tiles;
+        count = tiles;
+    }
+    return total + 1;
+}
+
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *tmp,
+                               int64_t tmp_elems, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    const int64_t tiles = (count + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_scan_tile_apply<<<1, kBlock, 0, s>>>(in, out, count, nullptr);
+        return cudaGetLastError();
+    }
+    if (tmp_elems < 2 * tiles) return cudaErrorInvalidValue;
+    int64_t *sums = tmp, *offs = tmp + tiles;
+    k_scan_tile_sums<<<(unsigned)tiles, kBlock, 0, s>>>(in, count, sums);
+    cudaError_t err = scan_exclusive_i64(sums, offs, tiles, tmp + 2 * tiles,
+                                         tmp_elems - 2 * tiles, s);
+    if (err != cudaSuccess) return err;
+    k_scan_tile_apply<<<(unsigned)tiles, kBlock, 0, s>>>(in, out, count, offs);
+    return cudaGetLastError();
+}
+
+int64_t classify_blocks(int64_t n) { return (n + kClassTile - 1) / kClassTile; }
+
+cudaError_t launch_classify(const Plan &p, int32_t d_small, int32_t d_hub, int64_t *blk_counts,
+                            int64_t *blk_offs, int64_t *tmp, int64_t tmp_elems, int32_t *nodes,
+                            int64_t *totals_dev, cudaStream_t s)
+{
+    const int64_t nt = classify_blocks(p.n);
+    if (nt == 0) return cudaSuccess;
+    k_class_count<<<(unsigned)nt, kBlock, 0, s>>>(p, d_small, d_hub, blk_counts, nt);
+    // one scan over [small tiles | medium tiles | hub tiles] lays the three
+    // lists out back to back; entry 3*nt is the total
+    cudaMemsetAsync(blk_counts + 3 * nt, 0, sizeof(int64_t), s);
+    cudaError_t err = scan_exclusive_i64(blk_counts, blk_offs, 3 * nt + 1, tmp, tmp_elems, s);
+    if (err != cudaSuccess) return err;
+    k_class_scatter<<<(unsigned)nt, kBlock, 0, s>>>(p, d_small, d_hub, blk_offs, nt, nodes);
+    // totals: start of medium, start of hub, end
+    cudaMemcpyAsync(totals_dev + 0, blk_offs + nt, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(totals_dev + 1, blk_offs + 2 * nt, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(totals_dev + 2, blk_offs + 3 * nt, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hub_segments(const Plan &p, int32_t d_hub, int64_t *seg_counts,
+                                int64_t *seg_offs, int64_t *tmp, int64_t tmp_elems,
+                                int32_t *seg_node, int64_t *seg_beg, int64_t *seg_end,
+                                int32_t *hub_seg_first, int64_t *total_dev, cudaStream_t s)
+{
+    const int32_t *hubs = p.nodes + p.n_small + p.n_med;
+    k_hub_seg_count<<<grid_for(p.n_hub + 1, kBlock), kBlock, 0, s>>>(p, d_hub, hubs, p.n_hub,
+                                                                     seg_counts);
+    cudaError_t err = scan_exclusive_i64(seg_counts, seg_offs, p.n_hub + 1, tmp, tmp_elems, s);
+    if (err != cudaSuccess) return err;
+    k_hub_seg_fill<<<grid_for(p.n_hub + 1, kBlock), kBlock, 0, s>>>(
+        p, d_hub, hubs, p.n_hub, seg_offs, seg_node, seg_beg, seg_end, hub_seg_first);
+    cudaMemcpyAsync(total_dev, seg_offs + p.n_hub, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const Plan &p, int64_t *in_off, int32_t *in_src, int64_t *cursor,
+                             int64_t *tmp, int64_t tmp_elems, cudaStream_t s)
+{
+    cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (p.n + 1), s);
+    k_in_degree<<<grid_for(p.arcs, kBlock, 152 * 64), kBlock, 0, s>>>(
+        p, reinterpret_cast<unsigned long long *>(cursor));
+    cudaError_t err = scan_exclusive_i64(cursor, in_off, p.n + 1, tmp, tmp_elems, s);
+    if (err != cudaSuccess) return err;
+    cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (p.n + 1), s);
+    k_transpose_fill<<<152 * 16, kBlock, 0, s>>>(p, in_off,
+                                                 reinterpret_cast<unsigned long long *>(cursor),
+                                                 in_src);
+    return cudaGetLastError();
+}
+
+}  // namespace hanf

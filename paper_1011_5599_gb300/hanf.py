@@ -1,0 +1,243 @@
+"""Thin ctypes binding of ``libhanf.so`` (declared in ``include/hanf.h``).
+
+Argument marshalling only: every step of HyperANF runs in the CUDA library.
+PyTorch provides the device workspace the library carves its buffers from and
+the stream it launches on.  If the library has not been built, every entry
+point raises ``HanfError`` -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhanf.so")
+
+HANF_OK, HANF_EINVAL, HANF_ENOMEM, HANF_ECUDA, HANF_ERANGE, HANF_ESTATE = 0, -1, -2, -3, -4, -5
+FRONTIER = {"off": 0, "pull": 1, "auto": 2}
+
+# Every function declared in include/hanf.h.
+EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
+           "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
+           "hanf_stats", "hanf_destroy", "hanf_last_error")
+
+COUNTER_NAMES = ("passes", "arcs_scanned", "arcs_gathered", "own_reads", "writes",
+                 "union_launches", "union_ms", "launches", "estimate_ms", "push_passes")
+
+
+class HanfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hanf error {code}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("runs", ctypes.c_int32), ("frontier", ctypes.c_int32),
+                ("push_den", ctypes.c_int32), ("small_max_deg", ctypes.c_int32),
+                ("hub_min_deg", ctypes.c_int32), ("history_cap", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("seeds", ctypes.POINTER(ctypes.c_uint64)), ("stream", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+_vp, _i32, _i64, _u64, _f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                               ctypes.c_uint64, ctypes.c_double)
+
+
+def lib():
+    """The loaded library (raises HanfError if it was never built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise HanfError(HANF_ESTATE, f"{LIB_PATH} is missing: build it with "
+                                         "__graft_entry__.build() (CUDA path only, no fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.hanf_default_opts.restype = None
+        L.hanf_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.hanf_workspace_size.restype = _i32
+        L.hanf_workspace_size.argtypes = [_i64, _i64, _i32, ctypes.POINTER(Opts), _i32,
+                                          ctypes.POINTER(ctypes.c_size_t)]
+        L.hanf_create.restype = _i32
+        L.hanf_create.argtypes = [ctypes.POINTER(_vp), _i64, _i64, _vp, _vp, _i32, _i32, _u64,
+                                  ctypes.POINTER(Opts), _vp, ctypes.c_size_t]
+        L.hanf_estimate.restype = _i32
+        L.hanf_estimate.argtypes = [_vp, ctypes.POINTER(_f64)]
+        L.hanf_iterate.restype = _i32
+        L.hanf_iterate.argtypes = [_vp, ctypes.POINTER(_i64)]
+        L.hanf_run.restype = _i32
+        L.hanf_run.argtypes = [_vp, _i32, ctypes.POINTER(_f64), _i32, ctypes.POINTER(_i32)]
+        L.hanf_registers.restype = _i32
+        L.hanf_registers.argtypes = [_vp, _i32, _i64, _i64, _vp]
+        L.hanf_current_t.restype = _i32
+        L.hanf_current_t.argtypes = [_vp, ctypes.POINTER(_i32)]
+        L.hanf_counters.restype = _i32
+        L.hanf_counters.argtypes = [_vp, ctypes.POINTER(_f64), _i32]
+        L.hanf_stats.restype = _i32
+        L.hanf_stats.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _i32, ctypes.POINTER(_f64)]
+        L.hanf_destroy.restype = None
+        L.hanf_destroy.argtypes = [_vp]
+        L.hanf_last_error.restype = ctypes.c_char_p
+        L.hanf_last_error.argtypes = []
+        _lib = L
+        return L
+
+
+def check(rc: int):
+    if rc != HANF_OK:
+        raise HanfError(rc, lib().hanf_last_error().decode())
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    lib().hanf_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=0,
+              history_cap=0, use_graph=False, profile=False, seeds=None, stream=None):
+    o = default_opts()
+    o.runs = runs
+    o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
+    o.push_den = push_den
+    o.small_max_deg = small_max_deg
+    o.hub_min_deg = hub_min_deg
+    o.history_cap = history_cap
+    o.use_graph = int(bool(use_graph))
+    o.profile = int(bool(profile))
+    keep = None
+    if seeds is not None:
+        keep = (ctypes.c_uint64 * len(seeds))(*[int(s) & (2**64 - 1) for s in seeds])
+        o.seeds = ctypes.cast(keep, ctypes.POINTER(ctypes.c_uint64))
+    o.stream = stream
+    return o, keep
+
+
+def workspace_size(n, arcs, log2m, opts: Opts, copy_graph: bool) -> int:
+    out = ctypes.c_size_t()
+    check(lib().hanf_workspace_size(n, arcs, log2m, ctypes.byref(opts), int(copy_graph),
+                                    ctypes.byref(out)))
+    return out.value
+
+
+def stats(N, T=None, alpha=0.9, exclude_zero=False) -> dict:
+    N = np.ascontiguousarray(N, dtype=np.float64)
+    T = N.size - 1 if T is None else T
+    out = np.zeros(5, dtype=np.float64)
+    check(lib().hanf_stats(N.ctypes.data_as(ctypes.POINTER(_f64)), T, alpha, int(exclude_zero),
+                           out.ctypes.data_as(ctypes.POINTER(_f64))))
+    return {"ed": out[0], "ied": out[1], "mean": out[2], "var": out[3], "spid": out[4]}
+
+
+class HyperANF:
+    """One HyperANF context (Algorithm 2 over R seeded runs) on a CUDA device.
+
+    ``offsets``/``targets`` may be numpy arrays or host tensors (copied into
+    the workspace) or CUDA tensors (borrowed; kept referenced here).
+    """
+
+    def __init__(self, offsets, targets, log2m: int, seed: int = 0x5EED, *, runs: int = 1,
+                 frontier="auto", push_den: int = 4, small_max_deg: int = 0,
+                 hub_min_deg: int = 0, history_cap: int = 0, use_graph: bool = False,
+                 profile: bool = False, seeds=None, device=None, stream=None):
+        import torch
+
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        on_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
+        if on_dev:
+            self._off = offsets.to(torch.int64).contiguous()
+            self._tgt = targets.to(torch.int32).contiguous()
+            off_p, tgt_p = self._off.data_ptr(), self._tgt.data_ptr()
+            n, arcs = self._off.numel() - 1, self._tgt.numel()
+        else:
+            if isinstance(offsets, torch.Tensor):
+                self._off = offsets.to(torch.int64).contiguous()
+                self._tgt = targets.to(torch.int32).contiguous()
+                off_p, tgt_p = self._off.data_ptr(), self._tgt.data_ptr()
+                n, arcs = self._off.numel() - 1, self._tgt.numel()
+            else:
+                self._off = np.ascontiguousarray(offsets, dtype=np.int64)
+                self._tgt = np.ascontiguousarray(targets, dtype=np.int32)
+                off_p, tgt_p = self._off.ctypes.data, self._tgt.ctypes.data
+                n, arcs = self._off.size - 1, self._tgt.size
+            if arcs == 0:
+                tgt_p = None
+        self.n, self.arcs, self.log2m, self.m, self.R = n, arcs, log2m, 1 << log2m, runs
+        self._opts, self._seed_keep = make_opts(runs, frontier, push_den, small_max_deg,
+                                                hub_min_deg, history_cap, use_graph, profile,
+                                                seeds, self.stream.cuda_stream)
+        size = workspace_size(n, arcs, log2m, self._opts, not on_dev)
+        self.workspace_bytes = size
+        with torch.cuda.device(self.device):
+            self._ws = torch.empty(size, dtype=torch.uint8, device=self.device)
+        ctx = ctypes.c_void_p()
+        check(lib().hanf_create(ctypes.byref(ctx), n, arcs, off_p, tgt_p, int(on_dev), log2m,
+                                seed & (2**64 - 1), ctypes.byref(self._opts),
+                                self._ws.data_ptr(), size))
+        self._ctx = ctx
+
+    # -- Algorithm 2 -------------------------------------------------------
+    def estimate(self) -> np.ndarray:
+        out = np.zeros(self.R, dtype=np.float64)
+        check(lib().hanf_estimate(self._ctx, out.ctypes.data_as(ctypes.POINTER(_f64))))
+        return out
+
+    def iterate(self) -> int:
+        ch = ctypes.c_int64()
+        check(lib().hanf_iterate(self._ctx, ctypes.byref(ch)))
+        return ch.value
+
+    def run(self, max_iter: int = 4096, cap: int = 4096):
+        """Whole Algorithm 2.  Returns (list of N_r(0..T_r), array of T_r)."""
+        N = np.zeros((self.R, cap), dtype=np.float64)
+        T = np.zeros(self.R, dtype=np.int32)
+        check(lib().hanf_run(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)), cap,
+                             T.ctypes.data_as(ctypes.POINTER(_i32))))
+        return [N[r, :T[r] + 1].copy() for r in range(self.R)], T
+
+    def run_raw(self, N: np.ndarray, T: np.ndarray, max_iter: int = 4096) -> int:
+        """hanf_run into caller-provided arrays; returns the status code."""
+        return lib().hanf_run(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)),
+                              N.shape[1], T.ctypes.data_as(ctypes.POINTER(_i32)))
+
+    def registers(self, run: int = 0, first: int = 0, count: int | None = None) -> np.ndarray:
+        count = self.n - first if count is None else count
+        out = np.zeros((max(count, 1), self.m), dtype=np.uint8)
+        check(lib().hanf_registers(self._ctx, run, first, count, out.ctypes.data))
+        return out[:count]
+
+    @property
+    def t(self) -> int:
+        t = ctypes.c_int32()
+        check(lib().hanf_current_t(self._ctx, ctypes.byref(t)))
+        return t.value
+
+    def counters(self) -> dict:
+        out = np.zeros(len(COUNTER_NAMES), dtype=np.float64)
+        check(lib().hanf_counters(self._ctx, out.ctypes.data_as(ctypes.POINTER(_f64)),
+                                  len(COUNTER_NAMES)))
+        return dict(zip(COUNTER_NAMES, out.tolist()))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            lib().hanf_destroy(self._ctx)
+            self._ctx = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,186 @@
+"""CUDA path vs the CPU oracle, through the C ABI, on seeded inputs.
+
+The bar: registers bit-exact (after every pass and at stabilisation), the
+stopping pass T identical, and N(t) within 1e-12 relative.  Cases cover the
+smallest workload (directed ER, n = 10^4, 5*10^4 arcs, m = 16), every
+register count m = 16..256, every frontier policy, all three degree classes
+(lane group per node, warp per node, hub segments), R-run batching, the
+CUDA-graph driver, ragged and degenerate graphs, and invalid input.
+"""
+import numpy as np
+import pytest
+
+from paper_1011_5599_gb300 import graphs as G
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EED
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1011_5599_gb300 import build as B
+    B.build()
+    import paper_1011_5599_gb300.hanf as H
+    return H
+
+
+def check_run(H, O, off, tgt, log2m, seed=SEED, R=1, threads=4, **kw):
+    with H.HyperANF(off, tgt, log2m, seed, runs=R, **kw) as h:
+        N, T = h.run()
+        regs = [h.registers(r) for r in range(R)]
+        cnt = h.counters()
+    for r in range(R):
+        No, To, ro = O.hyperanf(off, tgt, log2m, O.run_seed(seed, r), want_regs=True,
+                                threads=threads)
+        assert T[r] == To, f"run {r}: T={T[r]} oracle {To}"
+        assert np.array_equal(regs[r], ro), f"run {r}: registers differ"
+        np.testing.assert_allclose(N[r], No, rtol=RTOL, atol=0)
+    return N, T, cnt
+
+
+def test_smallest_workload_er_m16(H, oracle):
+    """Directed ER n=10,000, 50,000 distinct arcs, m=16, one run."""
+    off, tgt = G.er(10000, 50000, seed=1)
+    for frontier in ("off", "pull", "auto"):
+        check_run(H, oracle, off, tgt, 4, frontier=frontier)
+
+
+@pytest.mark.parametrize("log2m", [4, 5, 6, 7, 8])
+@pytest.mark.parametrize("frontier", ["off", "pull", "auto"])
+def test_er_every_m_and_frontier(H, oracle, log2m, frontier):
+    off, tgt = G.er(3000, 12000, seed=log2m)
+    check_run(H, oracle, off, tgt, log2m, frontier=frontier)
+
+
+def test_every_pass_bit_exact(H, oracle):
+    """Step by step: registers and N(t) after every pass."""
+    off, tgt = G.web(1 << 13, seed=2)
+    log2m = 6
+    seed = SEED
+    c = oracle.init(off.size - 1, log2m, oracle.run_seed(seed, 0))
+    with H.HyperANF(off, tgt, log2m, seed) as h:
+        t = 0
+        while True:
+            assert h.t == t
+            assert np.array_equal(h.registers(0), c), f"t={t}"
+            np.testing.assert_allclose(h.estimate()[0], oracle.sum_sizes(c), rtol=RTOL)
+            changed = h.iterate()
+            c_next, ch_o = oracle.union_pass(off, tgt, c)
+            assert changed == ch_o, f"t={t}: changed {changed} vs {ch_o}"
+            if changed == 0:
+                assert np.array_equal(h.registers(0), c_next)
+                break
+            c = c_next
+            t += 1
+        assert h.iterate() == 0          # stable: further calls are no-ops
+
+
+@pytest.mark.parametrize("small,hub", [(1, 2), (1, 4), (2, 8), (4096, 1 << 20), (1, 1 << 20),
+                                       (0, 0)])
+def test_degree_classes(H, oracle, small, hub):
+    """Force nodes into lane-group, warp and hub-segment paths."""
+    off, tgt = G.web(1 << 12, seed=5)
+    for frontier in ("pull", "auto"):
+        check_run(H, oracle, off, tgt, 6, frontier=frontier, small_max_deg=small, hub_min_deg=hub)
+
+
+def test_rmat_hubs(H, oracle):
+    off, tgt = G.rmat(13, seed=3)
+    assert np.diff(off).max() > 1024       # has hub segments at the default split
+    check_run(H, oracle, off, tgt, 6, frontier="auto")
+    check_run(H, oracle, off, tgt, 7, frontier="pull", hub_min_deg=64)
+
+
+@pytest.mark.parametrize("R,log2m", [(2, 4), (4, 6), (8, 6), (8, 8), (2, 8)])
+def test_batched_runs(H, oracle, R, log2m):
+    off, tgt = G.web(1 << 12, seed=7)
+    check_run(H, oracle, off, tgt, log2m, R=R)
+
+
+def test_explicit_seeds(H, oracle):
+    off, tgt = G.er(2000, 6000, seed=9)
+    seeds = [11, 0xDEADBEEF, 2**63 + 5, 0]
+    with H.HyperANF(off, tgt, 6, 0, runs=4, seeds=seeds) as h:
+        N, T = h.run()
+        regs = [h.registers(r) for r in range(4)]
+    for r, s in enumerate(seeds):
+        No, To, ro = oracle.hyperanf(off, tgt, 6, s, want_regs=True)
+        assert T[r] == To and np.array_equal(regs[r], ro)
+        np.testing.assert_allclose(N[r], No, rtol=RTOL)
+
+
+def test_graph_driver_matches_host_loop(H, oracle):
+    off, tgt = G.web(1 << 13, seed=4)
+    a = check_run(H, oracle, off, tgt, 6, R=4, use_graph=False)
+    b = check_run(H, oracle, off, tgt, 6, R=4, use_graph=True)
+    for r in range(4):
+        assert np.array_equal(a[0][r], b[0][r])       # bit-identical N(t)
+    assert list(a[1]) == list(b[1])
+
+
+def test_repeated_runs_identical(H):
+    off, tgt = G.rmat(12, seed=8)
+    with H.HyperANF(off, tgt, 6, SEED, use_graph=True) as h:
+        N1, T1 = h.run()
+        N2, T2 = h.run()
+    assert list(T1) == list(T2) and np.array_equal(N1[0], N2[0])
+
+
+@pytest.mark.parametrize("name", ["path", "cycle", "star", "complete", "clique_path", "grid"])
+def test_closed_form_fixtures(H, oracle, name):
+    g = {"path": lambda: G.path(40), "cycle": lambda: G.cycle(33), "star": lambda: G.star(300),
+         "complete": lambda: G.complete(20), "clique_path": lambda: G.clique_path(35, 3),
+         "grid": lambda: G.grid2d(30)}[name]()
+    for frontier in ("off", "auto"):
+        check_run(H, oracle, *g, 8, frontier=frontier)
+
+
+def test_degenerate_graphs(H, oracle):
+    for n in (0, 1, 2, 65, 1000):
+        check_run(H, oracle, *G.empty(n), 6)
+    # self-loops and duplicate arcs are legal
+    off = np.array([0, 3, 5, 6, 6], dtype=np.int64)
+    tgt = np.array([0, 1, 1, 2, 2, 0], dtype=np.int32)
+    check_run(H, oracle, off, tgt, 4)
+    check_run(H, oracle, off, tgt, 8, R=8)
+
+
+def test_device_resident_graph(H, oracle):
+    import torch
+    off, tgt = G.er(5000, 20000, seed=12)
+    with H.HyperANF(torch.from_numpy(off).cuda(), torch.from_numpy(tgt).cuda(), 6, SEED) as h:
+        N, T = h.run()
+        regs = h.registers(0)
+    No, To, ro = oracle.hyperanf(off, tgt, 6, oracle.run_seed(SEED, 0), want_regs=True)
+    assert T[0] == To and np.array_equal(regs, ro)
+    np.testing.assert_allclose(N[0], No, rtol=RTOL)
+
+
+def test_invalid_csr_rejected(H):
+    off = np.array([0, 2, 3], dtype=np.int64)
+    with pytest.raises(H.HanfError) as e:
+        H.HyperANF(off, np.array([0, 5, 1], dtype=np.int32), 6)        # target out of range
+    assert e.value.code == H.HANF_EINVAL
+    with pytest.raises(H.HanfError) as e:
+        H.HyperANF(np.array([0, 2, 1, 3], dtype=np.int64), np.array([0, 1, 2], dtype=np.int32), 6)
+    assert e.value.code == H.HANF_EINVAL
+    with pytest.raises(H.HanfError) as e:
+        H.HyperANF(off, np.array([0, -1, 1], dtype=np.int32), 6)
+    assert e.value.code == H.HANF_EINVAL
+
+
+def test_history_exhausted(H, oracle):
+    off, tgt = G.path(50)
+    with H.HyperANF(off, tgt, 6, SEED) as h:
+        N = np.zeros((1, 10), dtype=np.float64)
+        T = np.zeros(1, dtype=np.int32)
+        assert h.run_raw(N, T, max_iter=4096) == H.HANF_ERANGE
+        No, _, _ = oracle.hyperanf(off, tgt, 6, oracle.run_seed(SEED, 0))
+        np.testing.assert_allclose(N[0, :10], No[:10], rtol=RTOL)
+        N2, T2 = h.run()                  # the context stays usable
+        assert T2[0] == len(No) - 1
