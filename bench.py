@@ -42,6 +42,10 @@ WORKLOADS = {
                    text="directed R-MAT scale 27, edge factor 16 (a,b,c,d = .57,.19,.19,.05, "
                         "scrambled labels, loops and duplicate arcs removed), m=64 byte "
                         "registers, 1 run, frontier auto"),
+    "rmat22": dict(kind="rmat", scale=22, ef=16, sym=False, log2m=6, runs=1,
+                   text="directed R-MAT scale 22, edge factor 16, m=64, 1 run (profiling case)"),
+    "rmat24": dict(kind="rmat", scale=24, ef=16, sym=False, log2m=6, runs=1,
+                   text="directed R-MAT scale 24, edge factor 16, m=64, 1 run (profiling case)"),
     "rmat24sym": dict(kind="rmat", scale=24, ef=16, sym=True, log2m=7, runs=1,
                       text="symmetrised R-MAT scale 24, edge factor 16, m=128, 1 run"),
     "web20": dict(kind="web", n=1 << 20, log2m=6, runs=8,
@@ -51,7 +55,9 @@ WORKLOADS = {
                text="directed ER n=10^4, 5*10^4 arcs, m=16, 1 run"),
 }
 # bounded CPU samples of the same recipes for the oracle
-CPU_SAMPLE = {"rmat27": dict(kind="rmat", scale=20, ef=16, sym=False),
+CPU_SAMPLE = {"rmat27": dict(kind="rmat", scale=21, ef=16, sym=False),
+              "rmat22": dict(kind="rmat", scale=18, ef=16, sym=False),
+              "rmat24": dict(kind="rmat", scale=19, ef=16, sym=False),
               "rmat24sym": dict(kind="rmat", scale=18, ef=16, sym=True),
               "web20": dict(kind="web", n=1 << 16),
               "er": dict(kind="er", n=10000, arcs=50000)}
@@ -236,6 +242,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -312,6 +319,12 @@ def main():
     else:
         elapsed_all, merges_all = elapsed, float(merges)
     value = merges_all / elapsed_all
+    if args.trace and args.driver == "host":
+        h.run()
+        for row in h.trace():
+            gbs = (4 * row["arcs_scanned"] + W * (row["arcs_gathered"] + row["own_reads"]
+                                                  + row["writes"])) / (row["union_ms"] * 1e6)
+            print(json.dumps({**row, "algorithmic_GBps": gbs}), file=sys.stderr)
     stat = {}
     try:
         from paper_1011_5599_gb300.hanf import stats

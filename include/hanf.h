@@ -70,7 +70,11 @@ typedef struct hanf_opts {
     int32_t history_cap;   /* capacity of the device N(t) history; 0 = 4096    */
     int32_t use_graph;     /* hanf_run: 1 = whole loop as one CUDA graph with a
                               device-side while node (no host syncs)           */
-    int32_t profile;       /* 1 = time every kernel launch with CUDA events    */
+    int32_t profile;       /* 1 = time the union kernels of every pass with
+                              CUDA events and keep a per-pass trace           */
+    int32_t dense_den;     /* while at least n/dense_den counters changed, a
+                              pull pass gathers every successor without
+                              testing the changed bitmap; 0 = 2               */
     const uint64_t *seeds; /* R explicit run seeds (host), or NULL             */
     void *stream;          /* cudaStream_t for every launch; NULL = default    */
 } hanf_opts;
@@ -134,6 +138,13 @@ HANF_API int hanf_current_t(hanf_ctx *ctx, int32_t *t_out);
  * else 0), out[7] all kernel launches, out[8] estimator milliseconds,
  * out[9] passes run in systolic (push) mode.  nout = entries wanted (<= 10). */
 HANF_API int hanf_counters(hanf_ctx *ctx, double *out, int32_t nout);
+
+/* Per-pass trace of the last run since initialisation (profile = 1 and the
+ * host-loop driver): up to max_rows rows of 8 doubles {t, mode (0 pull with
+ * the changed-bitmap test, 1 systolic push, 2 pull gathering every
+ * successor), nodes changed, union milliseconds, arcs scanned, arcs gathered,
+ * own counters read, counters written}; *rows_out = rows written. */
+HANF_API int hanf_trace(hanf_ctx *ctx, double *out, int32_t max_rows, int32_t *rows_out);
 
 /* Section 4 and 5 statistics of N(0..T) (host arrays, no GPU):
  * out5 = {effective diameter at alpha, interpolated effective diameter, mean

@@ -76,7 +76,7 @@ struct Sizes {
 };
 
 struct Layout {
-    size_t off, tgt, in_off, in_src, regs0, regs1, F0, F1, cand, list0, list1, nodes;
+    size_t off, tgt, in_off, in_src, regs0, regs1, F0, F1, cand, cand0, cand1, list0, list1, nodes;
     size_t seg_node, seg_beg, seg_end, hub_first, hub_part, hub_any;
     size_t blk_part, red_part, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
     size_t seg_counts, seg_offs, totals, total;
@@ -93,6 +93,7 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     if (o.frontier < HANF_FRONTIER_OFF || o.frontier > HANF_FRONTIER_AUTO)
         return fail(HANF_EINVAL, "frontier=%d invalid", o.frontier);
     if (o.push_den < 1) return fail(HANF_EINVAL, "push_den=%d < 1", o.push_den);
+    if (o.dense_den < 0) return fail(HANF_EINVAL, "dense_den=%d < 0", o.dense_den);
     if (o.small_max_deg < 0 || o.hub_min_deg < 0 || o.history_cap < 0)
         return fail(HANF_EINVAL, "negative tuning option");
     s->n = n;
@@ -140,6 +141,8 @@ Layout make_layout(const Sizes &s)
     L.F0 = take(8 * s.nwords);
     L.F1 = take(8 * s.nwords);
     L.cand = take(8 * s.nwords);
+    L.cand0 = s.transpose ? take(4 * rows) : 0;
+    L.cand1 = s.transpose ? take(4 * rows) : 0;
     L.list0 = take(4 * rows);
     L.list1 = take(4 * rows);
     L.nodes = take(4 * rows);
@@ -188,6 +191,7 @@ struct hanf_ctx {
     cudaGraphExec_t gexec;
     cudaStream_t capture_stream;
     std::vector<uint64_t> seeds;
+    std::vector<double> trace;   // 8 values per pass (hanf_trace)
 };
 
 namespace {
@@ -214,6 +218,7 @@ int reset(hanf_ctx *c, int32_t max_t)
     c->launches = nl;
     c->union_ms = 0;
     c->est_ms = 0;
+    c->trace.clear();
     CU(cudaStreamSynchronize(c->stream));   // h lives on this stack frame
     c->host_ctl = h;
     return HANF_OK;
@@ -222,6 +227,7 @@ int reset(hanf_ctx *c, int32_t max_t)
 int one_pass(hanf_ctx *c)
 {
     const bool prof = c->opts.profile != 0;
+    const DevCtl before = c->host_ctl;
     int nl = 0;
     CU(hanf::launch_pass(c->plan, c->stream, 0, 0, prof ? c->ev[0] : nullptr,
                          prof ? c->ev[1] : nullptr, &nl));
@@ -232,6 +238,16 @@ int one_pass(hanf_ctx *c)
         float ms = 0;
         CU(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
         c->union_ms += ms;
+        const DevCtl &a = c->host_ctl;
+        const double row[8] = {(double)before.t,
+                               (double)a.mode,
+                               (double)a.last_changed,
+                               (double)ms,
+                               (double)(a.arcs_scanned - before.arcs_scanned),
+                               (double)(a.arcs_gathered - before.arcs_gathered),
+                               (double)(a.own_reads - before.own_reads),
+                               (double)(a.writes - before.writes)};
+        c->trace.insert(c->trace.end(), row, row + 8);
     }
     return HANF_OK;
 }
@@ -274,7 +290,8 @@ int build_graph(hanf_ctx *c)
 
 int pass_launch_count(const hanf_ctx *c)
 {
-    return 4 + (c->plan.in_off ? 1 : 0) + (c->plan.n_hub ? 1 : 0) + 3;
+    const Plan &p = c->plan;
+    return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + 3;
 }
 
 }  // namespace
@@ -293,6 +310,7 @@ void hanf_default_opts(hanf_opts *o)
     o->history_cap = 0;
     o->use_graph = 0;
     o->profile = 0;
+    o->dense_den = 0;
     o->seeds = nullptr;
     o->stream = nullptr;
 }
@@ -356,6 +374,7 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.nred = s.nred;
     p.frontier = o.frontier;
     p.push_den = o.push_den;
+    p.dense_den = o.dense_den ? o.dense_den : 2;
     p.history_cap = s.history;
     cudaStream_t st = c->stream;
     if (s.copy_graph) {
@@ -378,6 +397,12 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.F[0] = reinterpret_cast<unsigned long long *>(ws + L.F0);
     p.F[1] = reinterpret_cast<unsigned long long *>(ws + L.F1);
     p.cand = reinterpret_cast<unsigned long long *>(ws + L.cand);
+    if (s.transpose) {
+        p.cand_list[0] = reinterpret_cast<int32_t *>(ws + L.cand0);
+        p.cand_list[1] = reinterpret_cast<int32_t *>(ws + L.cand1);
+    }
+    p.d_small = s.d_small;
+    p.d_hub = s.d_hub;
     p.list[0] = reinterpret_cast<int32_t *>(ws + L.list0);
     p.list[1] = reinterpret_cast<int32_t *>(ws + L.list1);
     int32_t *nodes = reinterpret_cast<int32_t *>(ws + L.nodes);
@@ -570,6 +595,16 @@ int hanf_counters(hanf_ctx *c, double *out, int32_t nout)
                           c->union_ms,             (double)c->launches,    c->est_ms,
                           (double)h.push_passes};
     for (int i = 0; i < nout && i < 10; ++i) out[i] = v[i];
+    return HANF_OK;
+}
+
+int hanf_trace(hanf_ctx *c, double *out, int32_t max_rows, int32_t *rows_out)
+{
+    if (!c || !rows_out || (max_rows > 0 && !out)) return fail(HANF_EINVAL, "NULL argument");
+    const int32_t rows = (int32_t)(c->trace.size() / 8);
+    const int32_t k = std::min(rows, std::max(max_rows, 0));
+    std::copy(c->trace.begin(), c->trace.begin() + 8 * (size_t)k, out);
+    *rows_out = k;
     return HANF_OK;
 }
 

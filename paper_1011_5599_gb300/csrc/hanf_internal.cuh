@@ -20,7 +20,7 @@ struct DevCtl {
     int32_t t;           // passes completed since initialisation
     int32_t parity;      // regs[parity] holds c_t, F[parity] the nodes changed into it
     int32_t done;        // 1 once a pass changed no counter
-    int32_t mode;        // 0 = pull, 1 = systolic push, for the coming pass
+    int32_t mode;        // coming pass: 0 pull + bitmap test, 1 systolic push, 2 dense pull
     int32_t max_t;       // stop (with err = HANF_ERANGE) after this many passes
     int32_t err;         // HANF_OK or HANF_ERANGE
     int32_t bad_graph;   // set by the CSR validator
@@ -29,6 +29,9 @@ struct DevCtl {
     unsigned long long list_count[2];        // length of changed-node list [parity]
     unsigned long long run_changed[kMaxRuns];
     unsigned long long last_changed;         // nodes changed by the last pass
+    unsigned long long cand_count[2];        // systolic candidates: small, medium degree
+    unsigned long long changed_in_arcs;      // sum of in-degrees of nodes changed this pass
+    unsigned long long last_changed_in_arcs; // same, for the last completed pass
     // work counters since initialisation
     unsigned long long passes, push_passes, arcs_scanned, arcs_gathered, own_reads, writes;
 };
@@ -47,6 +50,8 @@ struct Plan {
     uint8_t *regs[2];                 // ping-pong counter arrays, n x W bytes
     unsigned long long *F[2];         // changed-node bitmaps (parity-indexed)
     unsigned long long *cand;         // systolic candidates of the coming pass
+    int32_t *cand_list[2];            // the candidates, small / medium degree (hubs: by bit)
+    int32_t d_small, d_hub;           // degree class bounds
     int32_t *list[2];                 // changed-node lists (parity-indexed)
     const int32_t *nodes;             // [small | medium | hub] node lists
     int64_t n_small, n_med, n_hub;
@@ -63,7 +68,7 @@ struct Plan {
     const double *lc;                 // m+1 linear-counting values m ln(m/V)
     double amm;                       // alpha_m m^2
     const uint64_t *seeds;            // R run seeds
-    int32_t frontier, push_den;
+    int32_t frontier, push_den, dense_den;
     int32_t history_cap;
     int32_t union_warps;              // resident warps of the union launch
     DevCtl *ctl;

@@ -40,10 +40,26 @@ struct Row {
     uint4 v[VPL];
 };
 
+// Register-wise max of four byte registers (Section 3.3, union via broadword
+// programming).  Registers never exceed 31, so bit 7 of every byte is free and
+// serves as the guard bit of the paper's parallel compare: in
+// d = (a | 0x80..80) - b no byte borrows from its neighbour, and bit 7 of byte
+// i of d is set iff a_i >= b_i.  A byte permute that replicates each byte's
+// top bit turns d into the selection mask (0xff where a_i >= b_i), and the
+// result is (a & mask) | (b & ~mask).
+__device__ __forceinline__ uint32_t bmax(uint32_t a, uint32_t b)
+{
+    const uint32_t d = (a | 0x80808080u) - b;
+    uint32_t mask;
+    // prmt with selector nibbles 8..11: byte i of the result replicates the
+    // sign bit of byte i of d (the __byte_perm intrinsic ignores that bit)
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(mask) : "r"(d), "r"(0u), "r"(0xBA98u));
+    return (a & mask) | (b & ~mask);
+}
+
 __device__ __forceinline__ uint4 vmax4(uint4 a, uint4 b)
 {
-    return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z),
-                      __vmaxu4(a.w, b.w));
+    return make_uint4(bmax(a.x, b.x), bmax(a.y, b.y), bmax(a.z, b.z), bmax(a.w, b.w));
 }
 
 __device__ __forceinline__ bool veq(uint4 a, uint4 b)
@@ -91,10 +107,10 @@ __device__ __forceinline__ void row_warp_max(Row<LANES, VPL> &r)
     for (int s = LANES; s < 32; s <<= 1) {
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
-            r.v[k].x = __vmaxu4(r.v[k].x, __shfl_xor_sync(kFull, r.v[k].x, s));
-            r.v[k].y = __vmaxu4(r.v[k].y, __shfl_xor_sync(kFull, r.v[k].y, s));
-            r.v[k].z = __vmaxu4(r.v[k].z, __shfl_xor_sync(kFull, r.v[k].z, s));
-            r.v[k].w = __vmaxu4(r.v[k].w, __shfl_xor_sync(kFull, r.v[k].w, s));
+            r.v[k].x = bmax(r.v[k].x, __shfl_xor_sync(kFull, r.v[k].x, s));
+            r.v[k].y = bmax(r.v[k].y, __shfl_xor_sync(kFull, r.v[k].y, s));
+            r.v[k].z = bmax(r.v[k].z, __shfl_xor_sync(kFull, r.v[k].z, s));
+            r.v[k].w = bmax(r.v[k].w, __shfl_xor_sync(kFull, r.v[k].w, s));
         }
     }
 }
@@ -114,36 +130,100 @@ __device__ __forceinline__ bool test_bit(const unsigned long long *bits, int32_t
 
 // ---------------------------------------------------------------- union
 
-// Merge the counters of arcs e, e+stride, ... < end into acc (skipping
-// successors outside the changed set unless all_succ).  U arcs are in flight
-// per step so that each lane group keeps several gathers outstanding.
+// Pass flavours (DevCtl::mode, chosen by k_prep before every pass):
+//   kModeTest   pull: every node scans its arcs, gathering only successors
+//               that changed in the previous pass (bitmap F_t);
+//   kModePush   systolic: only candidate nodes (changed nodes and their
+//               predecessors) scan their arcs, gathering changed successors;
+//   kModeDense  pull without the per-arc test, used at t = 0, with the
+//               frontier off, and while most counters still change: merging an
+//               unchanged successor is harmless, max being idempotent.
+constexpr int kModeTest = 0;
+constexpr int kModePush = 1;
+constexpr int kModeDense = 2;
+
+// Gather the counters of arcs [beg, end) of one node, one lane group per
+// node (all lanes of the group share beg/end).  Each lane loads U/LANES
+// targets of a batch of U (one batch ahead), tests its own targets against
+// the changed bitmap, and the group then issues the U row gathers together.
 template <int LANES, int VPL, int U>
-__device__ __forceinline__ void gather(const int32_t *__restrict__ tgt, const uint8_t *rc,
-                                       const unsigned long long *Fc, bool all_succ, int64_t e,
-                                       int64_t end, int64_t stride, int gl,
-                                       Row<LANES, VPL> &acc, bool &any, uint32_t &gathered)
+__device__ __forceinline__ void group_gather(const int32_t *__restrict__ tgt, const uint8_t *rc,
+                                             const unsigned long long *Fc, bool test,
+                                             int64_t beg, int64_t end, int gl, unsigned gmask,
+                                             int gbase, Row<LANES, VPL> &acc, bool &any,
+                                             uint32_t &gathered)
 {
-    for (; e < end; e += U * stride) {
-        int32_t w[U];
-        bool tk[U];
+    constexpr int TPL = (U + LANES - 1) / LANES;
+    int32_t nxt[TPL];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t eu = e + u * stride;
-            w[u] = eu < end ? __ldg(tgt + eu) : -1;
+    for (int k = 0; k < TPL; ++k) {
+        const int j = gl + k * LANES;
+        nxt[k] = (j < U && beg + j < end) ? __ldg(tgt + beg + j) : -1;
+    }
+    for (int64_t e = beg; e < end; e += U) {
+        int32_t cur[TPL];
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            cur[k] = nxt[k];
+            const int j = gl + k * LANES;
+            nxt[k] = (j < U && e + U + j < end) ? __ldg(tgt + e + U + j) : -1;
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) tk[u] = w[u] >= 0 && (all_succ || test_bit(Fc, w[u]));
+        for (int k = 0; k < TPL; ++k)
+            if (cur[k] >= 0 && test && !test_bit(Fc, cur[k])) cur[k] = -1;
+        int32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            w[u] = LANES == 1 ? cur[u] : __shfl_sync(gmask, cur[u / LANES], gbase + (u % LANES));
         Row<LANES, VPL> x[U];
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (tk[u]) row_load(x[u], rc, w[u], gl);
+            if (w[u] >= 0) row_load(x[u], rc, w[u], gl);
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (tk[u]) {
+            if (w[u] >= 0) {
                 row_max(acc, x[u]);
                 any = true;
                 ++gathered;
             }
+    }
+}
+
+// Gather the counters of arcs [beg, end) with the whole warp (beg/end warp-
+// uniform).  Lane i loads target e+i of each batch of 32 (one batch ahead,
+// coalesced) and tests it; lane group g then merges the targets of lanes
+// g, g+GPW, ..., SUB rows in flight at a time.
+template <int LANES, int VPL>
+__device__ __forceinline__ void warp_gather(const int32_t *__restrict__ tgt, const uint8_t *rc,
+                                            const unsigned long long *Fc, bool test, int64_t beg,
+                                            int64_t end, int g, int gl, Row<LANES, VPL> &acc,
+                                            bool &any, uint32_t &gathered)
+{
+    constexpr int GPW = 32 / LANES;
+    constexpr int SUB = (8 / VPL) < LANES ? (8 / VPL) : LANES;
+    const int lane = threadIdx.x & 31;
+    int32_t nxt = beg + lane < end ? __ldg(tgt + beg + lane) : -1;
+    for (int64_t e = beg; e < end; e += 32) {
+        int32_t cur = nxt;
+        nxt = e + 32 + lane < end ? __ldg(tgt + e + 32 + lane) : -1;
+        if (cur >= 0 && test && !test_bit(Fc, cur)) cur = -1;
+        const unsigned live = __ballot_sync(kFull, cur >= 0);
+        if (live == 0) continue;
+        any = true;
+        gathered += __popc(live);
+#pragma unroll
+        for (int s = 0; s < LANES; s += SUB) {
+            int32_t w[SUB];
+#pragma unroll
+            for (int u = 0; u < SUB; ++u) w[u] = __shfl_sync(kFull, cur, (s + u) * GPW + g);
+            Row<LANES, VPL> x[SUB];
+#pragma unroll
+            for (int u = 0; u < SUB; ++u)
+                if (w[u] >= 0) row_load(x[u], rc, w[u], gl);
+#pragma unroll
+            for (int u = 0; u < SUB; ++u)
+                if (w[u] >= 0) row_max(acc, x[u]);
+        }
     }
 }
 
@@ -199,106 +279,134 @@ __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, i
         const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u));
         if (lane == 0 && br) atomicAdd(&p.ctl->run_changed[r], (unsigned long long)__popc(br));
     }
+    if (p.in_off) {
+        unsigned long long indeg = ch ? (unsigned long long)(__ldg(p.in_off + v + 1) - __ldg(p.in_off + v)) : 0ull;
+#pragma unroll
+        for (int s = 16; s; s >>= 1) indeg += __shfl_xor_sync(kFull, indeg, s);
+        if (lane == 0 && indeg) atomicAdd(&p.ctl->changed_in_arcs, indeg);
+    }
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
+__device__ __forceinline__ unsigned warp_sum_u32(unsigned x)
 {
 #pragma unroll
     for (int s = 16; s; s >>= 1) x += __shfl_xor_sync(kFull, x, s);
     return x;
 }
 
-// One union pass.  Work items, handed to warps round-robin: hub segments
-// (a warp merges up to hub_min_deg arcs into a partial row), then medium
-// nodes (a warp per node, lane groups striding over the arcs), then small
-// nodes (a lane group per node, GPW nodes per warp).
+__device__ __forceinline__ void flush_counters(const Plan &p, uint32_t scan, uint32_t gather,
+                                               uint32_t own, uint32_t write)
+{
+    const unsigned s0 = warp_sum_u32(scan), s1 = warp_sum_u32(gather);
+    const unsigned s2 = warp_sum_u32(own), s3 = warp_sum_u32(write);
+    if ((threadIdx.x & 31) == 0) {
+        DevCtl *c = p.ctl;
+        if (s0) atomicAdd(&c->arcs_scanned, (unsigned long long)s0);
+        if (s1) atomicAdd(&c->arcs_gathered, (unsigned long long)s1);
+        if (s2) atomicAdd(&c->own_reads, (unsigned long long)s2);
+        if (s3) atomicAdd(&c->writes, (unsigned long long)s3);
+    }
+}
+
+// Union pass over small nodes (degree <= small_max_deg): a lane group per
+// node, GPW nodes per warp, warps striding over the small-node list.
 template <int LANES, int VPL>
-__global__ void __launch_bounds__(kBlock) k_union(Plan p)
+__global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
 {
     constexpr int GPW = 32 / LANES;
-    constexpr int U = VPL >= 4 ? 2 : 4;
+    constexpr int U = 8 / VPL;
     const DevCtl *ctl = p.ctl;
     if (ctl->done) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
-    const bool all_succ = first || p.frontier == HANF_FRONTIER_OFF;
-    const bool push = ctl->mode == 1;
+    const bool test = ctl->mode != kModeDense;
+    const bool push = ctl->mode == kModePush;
+    const uint8_t *rc = p.regs[cur];
+    const unsigned long long *Fc = p.F[cur];
+    const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
+    const int gbase = g * LANES;
+    const unsigned gmask = LANES == 32 ? kFull : (((1u << LANES) - 1u) << gbase);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    // systolic passes visit the small-degree candidates only
+    const int32_t *list = push ? p.cand_list[0] : p.nodes;
+    const int64_t count = push ? (int64_t)ctl->cand_count[0] : p.n_small;
+    for (int64_t base = warp * GPW; base < count; base += nwarps * GPW) {
+        const int64_t idx = base + g;
+        const bool valid = idx < count;
+        const int32_t v = valid ? __ldg(list + idx) : 0;
+        const bool take = valid;
+        Row<LANES, VPL> acc;
+        row_zero(acc);
+        bool any = false;
+        if (take) {
+            const int64_t beg = __ldg(p.off + v), end = __ldg(p.off + v + 1);
+            group_gather<LANES, VPL, U>(p.tgt, rc, Fc, test, beg, end, gl, gmask, gbase, acc, any,
+                                        c_gather);
+            if (gl == 0) c_scan += (uint32_t)(end - beg);
+        }
+        const bool inR = take && !first && test_bit(Fc, v);
+        const bool need = take && (any || inR);
+        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+        warp_mark(p, cur, gl == 0 && valid, v, mask);
+    }
+    flush_counters(p, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
+}
+
+// Union pass over medium nodes (a warp per node) and hub segments (a warp
+// merges up to hub_min_deg arcs of a hub into a partial row, combined later
+// by k_hub_finish).  Hub segments come first so the longest items start
+// early.
+template <int LANES, int VPL>
+__global__ void __launch_bounds__(kBlock, 3) k_union_warp(Plan p)
+{
+    constexpr int GPW = 32 / LANES;
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const bool test = ctl->mode != kModeDense;
+    const bool push = ctl->mode == kModePush;
+    // systolic passes visit the medium-degree candidates only
+    const int32_t *med = push ? p.cand_list[1] : p.nodes + p.n_small;
+    const int64_t total = p.n_seg + (push ? (int64_t)ctl->cand_count[1] : p.n_med);
     const uint8_t *rc = p.regs[cur];
     const unsigned long long *Fc = p.F[cur];
     const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t n_small_items = (p.n_small + GPW - 1) / GPW;
-    const int64_t med_end = p.n_seg + p.n_med;
-    const int64_t total = med_end + n_small_items;
-    uint32_t c_gather = 0, c_own = 0, c_write = 0;
-    unsigned long long c_scan = 0;
-
+    uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     for (int64_t it = warp; it < total; it += nwarps) {
+        const bool seg = it < p.n_seg;
+        const int32_t v = seg ? __ldg(p.seg_node + it) : __ldg(med + (it - p.n_seg));
+        const bool take = !seg || !push || test_bit(p.cand, v);
         Row<LANES, VPL> acc;
         row_zero(acc);
         bool any = false;
-        if (it < p.n_seg) {
-            const int32_t v = p.seg_node[it];
-            const bool take = !push || test_bit(p.cand, v);
-            if (take) {
-                const int64_t beg = p.seg_beg[it], end = p.seg_end[it];
-                gather<LANES, VPL, U>(p.tgt, rc, Fc, all_succ, beg + g, end, GPW, gl, acc, any,
-                                      c_gather);
-                if (lane == 0) c_scan += end - beg;
-            }
-            row_warp_max(acc);
-            any = __any_sync(kFull, any);
+        if (take) {
+            const int64_t beg = seg ? __ldg(p.seg_beg + it) : __ldg(p.off + v);
+            const int64_t end = seg ? __ldg(p.seg_end + it) : __ldg(p.off + v + 1);
+            warp_gather<LANES, VPL>(p.tgt, rc, Fc, test, beg, end, g, gl, acc, any, c_gather);
+            if (lane == 0) c_scan += (uint32_t)(end - beg);
+        }
+        row_warp_max(acc);
+        any = __any_sync(kFull, any);
+        if (seg) {
             if (g == 0) row_store(p.hub_part, it, acc, gl);
             if (lane == 0) p.hub_any[it] = any ? 1 : 0;
-        } else if (it < med_end) {
-            const int32_t v = p.nodes[p.n_small + (it - p.n_seg)];
-            const bool take = !push || test_bit(p.cand, v);
-            if (take) {
-                const int64_t beg = __ldg(p.off + v), end = __ldg(p.off + v + 1);
-                gather<LANES, VPL, U>(p.tgt, rc, Fc, all_succ, beg + g, end, GPW, gl, acc, any,
-                                      c_gather);
-                if (lane == 0) c_scan += end - beg;
-            }
-            row_warp_max(acc);
-            any = __any_sync(kFull, any);
+        } else {
             const bool inR = take && !first && test_bit(Fc, v);
             const bool need = take && (any || inR) && g == 0;
             const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
             warp_mark(p, cur, lane == 0, v, mask);
-        } else {
-            const int64_t idx = (it - med_end) * GPW + g;
-            const bool valid = idx < p.n_small;
-            const int32_t v = valid ? p.nodes[idx] : 0;
-            const bool take = valid && (!push || test_bit(p.cand, v));
-            if (take) {
-                const int64_t beg = __ldg(p.off + v), end = __ldg(p.off + v + 1);
-                gather<LANES, VPL, U>(p.tgt, rc, Fc, all_succ, beg, end, 1, gl, acc, any,
-                                      c_gather);
-                if (gl == 0) c_scan += end - beg;
-            }
-            const bool inR = take && !first && test_bit(Fc, v);
-            const bool need = take && (any || inR);
-            const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
-            warp_mark(p, cur, gl == 0 && valid, v, mask);
         }
     }
-    // work counters: one atomic per warp and counter
-    const unsigned long long s_scan = warp_sum_u64(c_scan);
-    const unsigned long long s_gather = warp_sum_u64(gl == 0 ? c_gather : 0u);
-    const unsigned long long s_own = warp_sum_u64(c_own);
-    const unsigned long long s_write = warp_sum_u64(c_write);
-    if (lane == 0) {
-        DevCtl *c = p.ctl;
-        if (s_scan) atomicAdd(&c->arcs_scanned, s_scan);
-        if (s_gather) atomicAdd(&c->arcs_gathered, s_gather);
-        if (s_own) atomicAdd(&c->own_reads, s_own);
-        if (s_write) atomicAdd(&c->writes, s_write);
-    }
+    flush_counters(p, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
 }
 
-// Hub nodes: combine the segment partials written by k_union, then finish
-// like any other node.  A lane group per hub.
+// Hub nodes: combine the segment partials written by k_union_warp, then
+// finish like any other node.  A lane group per hub.
 template <int LANES, int VPL>
 __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
 {
@@ -307,7 +415,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
     if (ctl->done || p.n_hub == 0) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
-    const bool push = ctl->mode == 1;
+    const bool push = ctl->mode == kModePush;
     const unsigned long long *Fc = p.F[cur];
     const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -336,12 +444,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
         const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
         warp_mark(p, cur, gl == 0 && valid, v, mask);
     }
-    const unsigned long long s_own = warp_sum_u64(c_own);
-    const unsigned long long s_write = warp_sum_u64(c_write);
-    if (lane == 0) {
-        if (s_own) atomicAdd(&p.ctl->own_reads, s_own);
-        if (s_write) atomicAdd(&p.ctl->writes, s_write);
-    }
+    flush_counters(p, 0u, 0u, c_own, c_write);
 }
 
 // ---------------------------------------------------------------- pass control
@@ -353,10 +456,21 @@ __global__ void k_prep(Plan p)
 {
     DevCtl *c = p.ctl;
     if (c->done) return;
-    const int push = p.frontier == HANF_FRONTIER_AUTO && p.in_off != nullptr && c->t > 0 &&
-                     (long long)c->last_changed * p.push_den < p.n;
-    c->mode = push;
+    const long long changed = (long long)c->last_changed;
+    int mode = kModeTest;
+    if (c->t == 0 || p.frontier == HANF_FRONTIER_OFF)
+        mode = kModeDense;
+    else if (p.frontier == HANF_FRONTIER_AUTO && p.in_off != nullptr && changed * p.push_den < p.n)
+        mode = kModePush;
+    else if (p.in_off != nullptr
+                 ? (long long)c->last_changed_in_arcs * p.dense_den >= p.arcs
+                 : changed * p.dense_den >= p.n)
+        mode = kModeDense;   // most successors changed: skip the per-arc test
+    c->mode = mode;
     c->list_count[c->parity ^ 1] = 0;
+    c->cand_count[0] = 0;
+    c->cand_count[1] = 0;
+    c->changed_in_arcs = 0;
     for (int r = 0; r < kMaxRuns; ++r) c->run_changed[r] = 0;
 }
 
@@ -365,7 +479,7 @@ __global__ void k_clear(Plan p)
     const DevCtl *c = p.ctl;
     if (c->done) return;
     unsigned long long *fn = p.F[c->parity ^ 1];
-    const bool push = c->mode == 1;
+    const bool push = c->mode == kModePush;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.nwords;
          i += (int64_t)gridDim.x * blockDim.x) {
         fn[i] = 0ull;
@@ -374,11 +488,34 @@ __global__ void k_clear(Plan p)
 }
 
 // Systolic signalling: every node changed by the previous pass marks itself
-// and its predecessors (through the transposed graph) as candidates.
+// and its predecessors (through the transposed graph) as candidates.  The
+// first marking of a node appends it to the candidate list of its degree
+// class (warp-aggregated), so the union kernels visit candidates only; hubs
+// are found through their segments.
+__device__ __forceinline__ void cand_append(const Plan &p, bool fresh, int32_t u)
+{
+    int cls = -1;
+    if (fresh) {
+        const int64_t deg = __ldg(p.off + u + 1) - __ldg(p.off + u);
+        cls = deg <= p.d_small ? 0 : (deg <= p.d_hub ? 1 : -1);
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const unsigned bal = __ballot_sync(kFull, cls == k);
+        if (bal == 0) continue;
+        const int first = __ffs(bal) - 1;
+        unsigned long long base = 0;
+        if (lane == first) base = atomicAdd(&p.ctl->cand_count[k], (unsigned long long)__popc(bal));
+        base = __shfl_sync(kFull, base, first);
+        if (cls == k) p.cand_list[k][base + __popc(bal & ((1u << lane) - 1u))] = u;
+    }
+}
+
 __global__ void k_mark(Plan p)
 {
     const DevCtl *c = p.ctl;
-    if (c->done || c->mode != 1) return;
+    if (c->done || c->mode != kModePush) return;
     const int cur = c->parity;
     const int64_t cnt = (int64_t)c->list_count[cur];
     const int32_t *lst = p.list[cur];
@@ -387,11 +524,17 @@ __global__ void k_mark(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < cnt; i += nwarps) {
         const int32_t w = lst[i];
-        if (lane == 0) atomicOr(&p.cand[w >> 6], 1ull << (w & 63));
-        const int64_t beg = p.in_off[w], end = p.in_off[w + 1];
-        for (int64_t e = beg + lane; e < end; e += 32) {
-            const int32_t u = __ldg(p.in_src + e);
-            atomicOr(&p.cand[u >> 6], 1ull << (u & 63));
+        const int64_t beg = p.in_off[w], deg = p.in_off[w + 1] - beg;
+        // item 0 is w itself, item j >= 1 its (j-1)-th predecessor
+        for (int64_t j0 = 0; j0 <= deg; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const int32_t u = j == 0 ? w : (j <= deg ? __ldg(p.in_src + beg + j - 1) : -1);
+            bool fresh = false;
+            if (u >= 0) {
+                const unsigned long long bit = 1ull << (u & 63);
+                fresh = (atomicOr(&p.cand[u >> 6], bit) & bit) == 0ull;
+            }
+            cand_append(p, fresh, u);
         }
     }
 }
@@ -406,8 +549,9 @@ __global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
         const int nxt = c->parity ^ 1;
         const unsigned long long changed = c->list_count[nxt];
         c->last_changed = changed;
+        c->last_changed_in_arcs = c->changed_in_arcs;
         c->passes += 1;
-        if (c->mode == 1) c->push_passes += 1;
+        if (c->mode == kModePush) c->push_passes += 1;
         for (int r = 0; r < p.R; ++r)
             if (c->T_run[r] < 0 && c->run_changed[r] == 0) c->T_run[r] = c->t;
         if (changed == 0) {
@@ -729,14 +873,22 @@ __global__ void k_in_degree(Plan p, unsigned long long *cnt)
 __global__ void k_transpose_fill(Plan p, const int64_t *in_off, unsigned long long *cursor,
                                  int32_t *in_src)
 {
+    constexpr int UF = 4;
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t v = warp; v < p.n; v += nwarps) {
-        for (int64_t e = p.off[v] + lane; e < p.off[v + 1]; e += 32) {
-            const int32_t w = p.tgt[e];
-            const unsigned long long k = atomicAdd(&cursor[w], 1ull);
-            in_src[in_off[w] + (int64_t)k] = (int32_t)v;
+        const int64_t beg = p.off[v], end = p.off[v + 1];
+        for (int64_t e0 = beg + lane; e0 < end; e0 += 32 * UF) {
+            int32_t w[UF];
+            unsigned long long k[UF];
+#pragma unroll
+            for (int u = 0; u < UF; ++u) w[u] = e0 + 32 * u < end ? __ldg(p.tgt + e0 + 32 * u) : -1;
+#pragma unroll
+            for (int u = 0; u < UF; ++u) k[u] = w[u] >= 0 ? atomicAdd(&cursor[w[u]], 1ull) : 0ull;
+#pragma unroll
+            for (int u = 0; u < UF; ++u)
+                if (w[u] >= 0) in_src[in_off[w[u]] + (int64_t)k[u]] = (int32_t)v;
         }
     }
 }
@@ -756,7 +908,8 @@ struct UnionKernels {
     static cudaError_t launch(const Plan &p, cudaStream_t s)
     {
         const int blocks = (p.union_warps * 32 + kBlock - 1) / kBlock;
-        k_union<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+        k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+        k_union_small<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
         return cudaGetLastError();
     }
     static cudaError_t launch_hub(const Plan &p, cudaStream_t s)
@@ -768,9 +921,10 @@ struct UnionKernels {
     }
     static int occupancy()
     {
-        int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_union<LANES, VPL>, kBlock, 0);
-        return nb;
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_union_small<LANES, VPL>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_union_warp<LANES, VPL>, kBlock, 0);
+        return a < b ? a : b;
     }
 };
 
@@ -841,7 +995,8 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     }
     if (ev1) cudaEventRecord(ev1, s);
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
-    if (nlaunch) *nlaunch += 4 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0);
+    if (nlaunch)
+        *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_estimate(p, s, nlaunch);

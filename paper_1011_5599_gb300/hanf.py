@@ -22,7 +22,9 @@ FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 # Every function declared in include/hanf.h.
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
            "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
-           "hanf_stats", "hanf_destroy", "hanf_last_error")
+           "hanf_trace", "hanf_stats", "hanf_destroy", "hanf_last_error")
+TRACE_NAMES = ("t", "mode", "changed", "union_ms", "arcs_scanned", "arcs_gathered", "own_reads",
+               "writes")
 
 COUNTER_NAMES = ("passes", "arcs_scanned", "arcs_gathered", "own_reads", "writes",
                  "union_launches", "union_ms", "launches", "estimate_ms", "push_passes")
@@ -39,6 +41,7 @@ class Opts(ctypes.Structure):
                 ("push_den", ctypes.c_int32), ("small_max_deg", ctypes.c_int32),
                 ("hub_min_deg", ctypes.c_int32), ("history_cap", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("dense_den", ctypes.c_int32),
                 ("seeds", ctypes.POINTER(ctypes.c_uint64)), ("stream", ctypes.c_void_p)]
 
 
@@ -78,6 +81,8 @@ def lib():
         L.hanf_current_t.argtypes = [_vp, ctypes.POINTER(_i32)]
         L.hanf_counters.restype = _i32
         L.hanf_counters.argtypes = [_vp, ctypes.POINTER(_f64), _i32]
+        L.hanf_trace.restype = _i32
+        L.hanf_trace.argtypes = [_vp, ctypes.POINTER(_f64), _i32, ctypes.POINTER(_i32)]
         L.hanf_stats.restype = _i32
         L.hanf_stats.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _i32, ctypes.POINTER(_f64)]
         L.hanf_destroy.restype = None
@@ -100,7 +105,8 @@ def default_opts() -> Opts:
 
 
 def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=0,
-              history_cap=0, use_graph=False, profile=False, seeds=None, stream=None):
+              history_cap=0, use_graph=False, profile=False, seeds=None, stream=None,
+              dense_den=0):
     o = default_opts()
     o.runs = runs
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
@@ -110,6 +116,7 @@ def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=
     o.history_cap = history_cap
     o.use_graph = int(bool(use_graph))
     o.profile = int(bool(profile))
+    o.dense_den = dense_den
     keep = None
     if seeds is not None:
         keep = (ctypes.c_uint64 * len(seeds))(*[int(s) & (2**64 - 1) for s in seeds])
@@ -144,7 +151,8 @@ class HyperANF:
     def __init__(self, offsets, targets, log2m: int, seed: int = 0x5EED, *, runs: int = 1,
                  frontier="auto", push_den: int = 4, small_max_deg: int = 0,
                  hub_min_deg: int = 0, history_cap: int = 0, use_graph: bool = False,
-                 profile: bool = False, seeds=None, device=None, stream=None):
+                 profile: bool = False, seeds=None, device=None, stream=None,
+                 dense_den: int = 0):
         import torch
 
         self.device = torch.device(device if device is not None else "cuda")
@@ -171,7 +179,7 @@ class HyperANF:
         self.n, self.arcs, self.log2m, self.m, self.R = n, arcs, log2m, 1 << log2m, runs
         self._opts, self._seed_keep = make_opts(runs, frontier, push_den, small_max_deg,
                                                 hub_min_deg, history_cap, use_graph, profile,
-                                                seeds, self.stream.cuda_stream)
+                                                seeds, self.stream.cuda_stream, dense_den)
         size = workspace_size(n, arcs, log2m, self._opts, not on_dev)
         self.workspace_bytes = size
         with torch.cuda.device(self.device):
@@ -223,6 +231,14 @@ class HyperANF:
         check(lib().hanf_counters(self._ctx, out.ctypes.data_as(ctypes.POINTER(_f64)),
                                   len(COUNTER_NAMES)))
         return dict(zip(COUNTER_NAMES, out.tolist()))
+
+    def trace(self) -> list:
+        """Per-pass rows of the last run (profile=True, host-loop driver)."""
+        rows = ctypes.c_int32()
+        out = np.zeros((4096, len(TRACE_NAMES)), dtype=np.float64)
+        check(lib().hanf_trace(self._ctx, out.ctypes.data_as(ctypes.POINTER(_f64)), 4096,
+                               ctypes.byref(rows)))
+        return [dict(zip(TRACE_NAMES, r.tolist())) for r in out[:rows.value]]
 
     def close(self):
         if getattr(self, "_ctx", None):
