@@ -152,6 +152,26 @@ HANF_API int hanf_trace(hanf_ctx *ctx, double *out, int32_t max_rows, int32_t *r
  * h(t) = H(t) - H(t-1); exclude_zero = 1 leaves out the pairs (x, x). */
 HANF_API int hanf_stats(const double *N, int32_t T, double alpha, int32_t exclude_zero, double *out5);
 
+/* Allocation-free estimate of N = sum_v size(c[v]) for a register array the
+ * caller already holds (the paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory while they run, such as a
+ * serving loop whose device memory was all reserved up front, or a process
+ * sharing the GPU with an allocator that owns all of it, where cudaMalloc
+ * would fail or synchronise the device).
+ *   regs: device pointer to n rows of runs * 2^log2m bytes (row v holds run 0's
+ *     registers, then run 1's, ...; values 0..31), the layout this library keeps.
+ *   N_out: device pointer to `runs` doubles, N for each run.
+ *   stream: cudaStream_t (NULL = default stream); the call only enqueues work.
+ * Its scratch is one fixed array of 2^20 doubles (8 MiB) inside the library,
+ * kept by every GPU that loads it until the process exits; runs * (ceil(n/64)
+ * + ceil(n/262144)) must not exceed 2^20, otherwise it returns HANF_EINVAL.
+ * The first call on each device looks the array's address up (once, with that
+ * device current), so make it before any stream capture.  Calls share the
+ * array and each overwrites what it reads; calls that overlap on the GPU race
+ * and must be serialised by the caller. */
+HANF_API int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2m, int32_t runs,
+                                  double *N_out, void *stream);
+
 /* Release the context (not the workspace, which belongs to the caller). */
 HANF_API void hanf_destroy(hanf_ctx *ctx);
 

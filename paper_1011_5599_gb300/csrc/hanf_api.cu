@@ -20,8 +20,12 @@ using hanf::DevCtl;
 using hanf::Plan;
 
 namespace {
-
 thread_local std::string g_err;
+}
+
+void hanf::record_error(const char *msg) { g_err = msg; }
+
+namespace {
 
 int fail(int code, const char *fmt, ...)
 {

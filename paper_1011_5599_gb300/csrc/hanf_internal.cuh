@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "hanf.h"
 
 namespace hanf {
@@ -96,5 +98,9 @@ cudaError_t launch_hub_segments(const Plan &p, int32_t d_hub, int64_t *seg_count
 cudaError_t launch_transpose(const Plan &p, int64_t *in_off, int32_t *in_src, int64_t *cursor,
                              int64_t *tmp, int64_t tmp_elems, cudaStream_t s);
 int64_t classify_blocks(int64_t n);
+
+// Store the calling thread's message for hanf_last_error().
+void record_error(const char *msg);
+inline void record_error(const std::string &msg) { record_error(msg.c_str()); }
 
 }  // namespace hanf

@@ -22,7 +22,7 @@ FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 # Every function declared in include/hanf.h.
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
            "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
-           "hanf_trace", "hanf_stats", "hanf_destroy", "hanf_last_error")
+           "hanf_trace", "hanf_stats", "hanf_estimate_static", "hanf_destroy", "hanf_last_error")
 TRACE_NAMES = ("t", "mode", "changed", "union_ms", "arcs_scanned", "arcs_gathered", "own_reads",
                "writes")
 
@@ -85,6 +85,8 @@ def lib():
         L.hanf_trace.argtypes = [_vp, ctypes.POINTER(_f64), _i32, ctypes.POINTER(_i32)]
         L.hanf_stats.restype = _i32
         L.hanf_stats.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _i32, ctypes.POINTER(_f64)]
+        L.hanf_estimate_static.restype = _i32
+        L.hanf_estimate_static.argtypes = [_vp, _i64, _i32, _i32, _vp, _vp]
         L.hanf_destroy.restype = None
         L.hanf_destroy.argtypes = [_vp]
         L.hanf_last_error.restype = ctypes.c_char_p
@@ -139,6 +141,20 @@ def stats(N, T=None, alpha=0.9, exclude_zero=False) -> dict:
     check(lib().hanf_stats(N.ctypes.data_as(ctypes.POINTER(_f64)), T, alpha, int(exclude_zero),
                            out.ctypes.data_as(ctypes.POINTER(_f64))))
     return {"ed": out[0], "ied": out[1], "mean": out[2], "var": out[3], "spid": out[4]}
+
+
+def estimate_static(regs, n: int, log2m: int, runs: int, out, stream=None) -> None:
+    """hanf_estimate_static: N of a device register array without allocating.
+
+    ``regs`` is a CUDA uint8 tensor of n rows of runs * 2^log2m bytes and
+    ``out`` a CUDA float64 tensor of ``runs`` values; the call only enqueues
+    the work on ``stream`` (default: torch's current stream)."""
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream(regs.device)
+    check(lib().hanf_estimate_static(regs.data_ptr() if n > 0 else None, n, log2m, runs,
+                                     out.data_ptr(), stream.cuda_stream))
 
 
 class HyperANF:
