@@ -277,6 +277,53 @@ ORA_API void ora_ball_registers(const int64_t *off, const int32_t *tgt, int64_t 
     free(queue);
 }
 
+/* Final sum N(T) of a symmetric graph (every arc u->w has w->u): the ball
+ * of v at stabilisation is v's connected component, so c_T[v] is the
+ * register-wise maximum of the singleton counters of the component.  The
+ * components are found by breadth-first search; the result is the
+ * Neumaier-compensated sum of size(c_T[v]) over v = 0..n-1, the same sum
+ * Algorithm 2 prints last.  Returns -1.0 on allocation failure. */
+ORA_API double ora_symmetric_final_sum(const int64_t *off, const int32_t *tgt, int64_t n,
+                                              int32_t b, uint64_t seed)
+{
+    int32_t m = 1 << b;
+    int64_t *comp = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    int64_t *queue = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+    uint8_t *creg = NULL;
+    double *csize = NULL;
+    int64_t ncomp = 0, v;
+    double s = 0.0, c = 0.0;
+    if (!comp || !queue) { free(comp); free(queue); return -1.0; }
+    for (v = 0; v < n; ++v) comp[v] = -1;
+    for (v = 0; v < n; ++v) {
+        int64_t head = 0, tail = 0;
+        if (comp[v] >= 0) continue;
+        comp[v] = ncomp;
+        queue[tail++] = v;
+        while (head < tail) {
+            int64_t u = queue[head++], e;
+            for (e = off[u]; e < off[u + 1]; ++e) {
+                int32_t w = tgt[e];
+                if (comp[w] < 0) { comp[w] = ncomp; queue[tail++] = w; }
+            }
+        }
+        ++ncomp;
+    }
+    creg = (uint8_t *)calloc((size_t)(ncomp ? ncomp : 1) * (size_t)m, 1);
+    csize = (double *)malloc((size_t)(ncomp ? ncomp : 1) * sizeof(double));
+    if (!creg || !csize) { free(comp); free(queue); free(creg); free(csize); return -1.0; }
+    for (v = 0; v < n; ++v) ora_add(creg + comp[v] * m, b, (uint64_t)v, seed);
+    for (v = 0; v < ncomp; ++v) csize[v] = ora_size(creg + v * m, m);
+    for (v = 0; v < n; ++v) {
+        double x = csize[comp[v]], t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    free(comp); free(queue); free(creg); free(csize);
+    return s + c;
+}
+
 /* ------------------------------------------------------------------ */
 /* Section 4 and Section 5: statistics read off N(0..T).               */
 /* ------------------------------------------------------------------ */

@@ -82,6 +82,9 @@ def _load():
         lib.ora_ball_registers.argtypes = [_i64p, _i32p, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                            _u8p]
+        lib.ora_symmetric_final_sum.restype = ctypes.c_double
+        lib.ora_symmetric_final_sum.argtypes = [_i64p, _i32p, ctypes.c_int64, ctypes.c_int32,
+                                                ctypes.c_uint64]
         lib.ora_stats.restype = None
         lib.ora_stats.argtypes = [_f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                   _f64p]
@@ -199,6 +202,15 @@ def ball_registers(offsets, targets, v: int, r: int, b: int, seed: int) -> np.nd
     _load().ora_ball_registers(_p(off, _i64p), _p(tgt, _i32p), n, v, r, b,
                                seed & (2**64 - 1), _p(out, _u8p))
     return out
+
+
+def symmetric_final_sum(offsets, targets, b: int, seed: int) -> float:
+    """N(T) of a symmetric graph from its connected components."""
+    off, tgt, n = _csr(offsets, targets)
+    r = _load().ora_symmetric_final_sum(_p(off, _i64p), _p(tgt, _i32p), n, b, seed & (2**64 - 1))
+    if r < 0:
+        raise MemoryError("oracle allocation failed")
+    return float(r)
 
 
 # --------------------------------------------------------------------------

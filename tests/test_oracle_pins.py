@@ -345,3 +345,28 @@ def test_stats_star_and_complete(oracle):
     # all mass at t = 0: effective diameter 0
     s = oracle.stats(np.array([5.0]))
     assert s["ed"] == 0 and s["ied"] == 0 and s["mean"] == 0
+
+
+@pytest.mark.parametrize("name", ["star", "grid", "er_sym", "two_components"])
+def test_symmetric_final_sum_equals_algorithm2(oracle, name):
+    """On a symmetric graph the stabilised counters are component unions, so
+    the component-based sum equals N(T) of the iteration."""
+    if name == "star":
+        off, tgt = G.star(50)
+    elif name == "grid":
+        off, tgt = G.grid2d(12)
+    elif name == "er_sym":
+        o, t = G.er(200, 300, seed=4)
+        src = np.repeat(np.arange(200), np.diff(o))
+        off, tgt = G.csr_from_arcs(np.concatenate([src, t]), np.concatenate([t, src]), 200)
+    else:
+        a, b = G.cycle(30), G.star(20)
+        src = np.concatenate([np.repeat(np.arange(30), np.diff(a[0])),
+                              30 + np.repeat(np.arange(20), np.diff(b[0]))])
+        dst = np.concatenate([a[1], 30 + b[1]])
+        src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
+        off, tgt = G.csr_from_arcs(src, dst, 50)
+    for s in range(5):
+        seed = oracle.run_seed(SEED, s)
+        N, T, _ = oracle.hyperanf(off, tgt, 6, seed)
+        assert oracle.symmetric_final_sum(off, tgt, 6, seed) == pytest.approx(N[-1], rel=1e-14)
