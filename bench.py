@@ -243,6 +243,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
+    ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -279,7 +280,8 @@ def main():
     stream = torch.cuda.current_stream(device)
 
     h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
-                 use_graph=args.driver == "graph", profile=args.driver == "host")
+                 use_graph=args.driver == "graph", profile=args.driver == "host",
+                 gather_variant=args.gather_variant)
     for _ in range(args.warmup):
         h.run()
 

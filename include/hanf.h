@@ -75,6 +75,13 @@ typedef struct hanf_opts {
     int32_t dense_den;     /* while at least n/dense_den counters changed, a
                               pull pass gathers every successor without
                               testing the changed bitmap; 0 = 2               */
+    int32_t relabel;       /* 1 = store the counters in decreasing in-degree
+                              order (hot counters share cache lines); results
+                              and hanf_registers use input ids either way    */
+    int32_t gather_variant;/* medium-degree nodes and hub segments gather rows
+                              with 0 = the default, 1 = register batches,
+                              2 = asynchronous copies into a shared-memory
+                              ring (rows of at most 128 bytes)                */
     const uint64_t *seeds; /* R explicit run seeds (host), or NULL             */
     void *stream;          /* cudaStream_t for every launch; NULL = default    */
 } hanf_opts;

@@ -48,6 +48,7 @@ int fail(int code, const char *fmt, ...)
 constexpr int32_t kDefaultSmall = 32;
 constexpr int32_t kDefaultHub = 1024;
 constexpr int32_t kDefaultHistory = 4096;
+constexpr int64_t kStageRows = 65536;   // rows per chunk of a relabelled register read
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -75,15 +76,16 @@ struct Sizes {
     int64_t n, arcs;
     int32_t log2m, m, R, W;
     int32_t d_small, d_hub, history;
-    bool copy_graph, transpose;
+    bool copy_graph, transpose, relabel;
     int64_t nwords, nred, ntiles, max_hub, max_seg, scan_elems;
 };
 
 struct Layout {
-    size_t off, tgt, in_off, in_src, regs0, regs1, F0, F1, cand, cand0, cand1, list0, list1, nodes;
+    size_t off, tgt, in_off, in_src, regs0, regs1, F0, F1, cand, cand0, cand1, nodes;
     size_t seg_node, seg_beg, seg_end, hub_first, hub_part, hub_any;
     size_t blk_part, red_part, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
-    size_t seg_counts, seg_offs, totals, total;
+    size_t seg_counts, seg_offs, totals, perm, inv, off2, tgt2, rcounts, roffs, stage;
+    size_t total;
 };
 
 int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32_t copy_graph,
@@ -98,6 +100,8 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
         return fail(HANF_EINVAL, "frontier=%d invalid", o.frontier);
     if (o.push_den < 1) return fail(HANF_EINVAL, "push_den=%d < 1", o.push_den);
     if (o.dense_den < 0) return fail(HANF_EINVAL, "dense_den=%d < 0", o.dense_den);
+    if (o.gather_variant < 0 || o.gather_variant > 2)
+        return fail(HANF_EINVAL, "gather_variant=%d invalid", o.gather_variant);
     if (o.small_max_deg < 0 || o.hub_min_deg < 0 || o.history_cap < 0)
         return fail(HANF_EINVAL, "negative tuning option");
     s->n = n;
@@ -116,12 +120,14 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     s->history = o.history_cap ? o.history_cap : kDefaultHistory;
     s->copy_graph = copy_graph != 0;
     s->transpose = o.frontier == HANF_FRONTIER_AUTO;
+    s->relabel = o.relabel != 0 && n > 0;
     s->nwords = std::max<int64_t>(1, (n + 63) / 64);
     s->nred = (s->nwords + hanf::kEstChunk - 1) / hanf::kEstChunk;
     s->ntiles = hanf::classify_blocks(n);
     s->max_hub = arcs / (s->d_hub + 1) + 1;
     s->max_seg = 2 * (arcs / s->d_hub) + 2;
-    int64_t biggest = std::max<int64_t>({n + 1, 3 * s->ntiles + 1, s->max_hub + 1});
+    int64_t biggest = std::max<int64_t>({n + 1, 3 * s->ntiles + 1, s->max_hub + 1,
+                                         hanf::relabel_count_elems(n)});
     s->scan_elems = hanf::scan_tmp_elems(biggest) * 2 + 64;
     return HANF_OK;
 }
@@ -147,8 +153,6 @@ Layout make_layout(const Sizes &s)
     L.cand = take(8 * s.nwords);
     L.cand0 = s.transpose ? take(4 * rows) : 0;
     L.cand1 = s.transpose ? take(4 * rows) : 0;
-    L.list0 = take(4 * rows);
-    L.list1 = take(4 * rows);
     L.nodes = take(4 * rows);
     L.seg_node = take(4 * s.max_seg);
     L.seg_beg = take(8 * s.max_seg);
@@ -168,6 +172,15 @@ Layout make_layout(const Sizes &s)
     L.seg_counts = take(8 * (s.max_hub + 1));
     L.seg_offs = take(8 * (s.max_hub + 1));
     L.totals = take(8 * 4);
+    if (s.relabel) {
+        L.perm = take(4 * rows);
+        L.inv = take(4 * rows);
+        L.off2 = take(8 * (s.n + 1));
+        L.tgt2 = take(4 * std::max<int64_t>(s.arcs, 1));
+        L.rcounts = take(8 * hanf::relabel_count_elems(s.n));
+        L.roffs = take(8 * hanf::relabel_count_elems(s.n));
+        L.stage = take((size_t)std::min<int64_t>(s.n, kStageRows) * s.W);
+    }
     L.total = at;
     return L;
 }
@@ -196,6 +209,8 @@ struct hanf_ctx {
     cudaStream_t capture_stream;
     std::vector<uint64_t> seeds;
     std::vector<double> trace;   // 8 values per pass (hanf_trace)
+    const int32_t *perm;         // input id -> stored row (relabelled), or null
+    uint8_t *stage;              // staging rows for relabelled register reads
 };
 
 namespace {
@@ -315,6 +330,8 @@ void hanf_default_opts(hanf_opts *o)
     o->use_graph = 0;
     o->profile = 0;
     o->dense_den = 0;
+    o->relabel = 1;
+    o->gather_variant = 0;
     o->seeds = nullptr;
     o->stream = nullptr;
 }
@@ -407,8 +424,6 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     }
     p.d_small = s.d_small;
     p.d_hub = s.d_hub;
-    p.list[0] = reinterpret_cast<int32_t *>(ws + L.list0);
-    p.list[1] = reinterpret_cast<int32_t *>(ws + L.list1);
     int32_t *nodes = reinterpret_cast<int32_t *>(ws + L.nodes);
     p.nodes = nodes;
     p.hub_part = ws + L.hub_part;
@@ -430,6 +445,28 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     if (c->host_ctl.bad_graph)
         return bail(fail(HANF_EINVAL, "invalid CSR: offsets must start at 0, end at arcs and "
                                       "not decrease; targets must lie in [0, n)"));
+
+    // 1b. store nodes by decreasing in-degree class: the relabelled CSR
+    //     replaces the input one for everything below
+    if (s.relabel) {
+        int32_t *perm = reinterpret_cast<int32_t *>(ws + L.perm);
+        int32_t *inv = reinterpret_cast<int32_t *>(ws + L.inv);
+        int64_t *off2 = reinterpret_cast<int64_t *>(ws + L.off2);
+        int32_t *tgt2 = reinterpret_cast<int32_t *>(ws + L.tgt2);
+        if (hanf::launch_relabel(p.off, p.tgt, n, arcs,
+                                 reinterpret_cast<unsigned long long *>(p.regs[1]),
+                                 reinterpret_cast<int64_t *>(ws + L.rcounts),
+                                 reinterpret_cast<int64_t *>(ws + L.roffs), scan_tmp, s.scan_elems,
+                                 perm, inv, reinterpret_cast<int64_t *>(p.regs[0]), off2,
+                                 tgt2, st) != cudaSuccess)
+            return bail(fail(HANF_ECUDA, "relabelling failed: %s",
+                             cudaGetErrorString(cudaGetLastError())));
+        p.off = off2;
+        p.tgt = tgt2;
+        p.orig_id = inv;
+        c->perm = perm;
+        c->stage = ws + L.stage;
+    }
 
     // 2. degree classes -> [small | medium | hub] node lists
     int64_t tot[4] = {0, 0, 0, 0};
@@ -491,6 +528,8 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
         return bail(fail(HANF_ECUDA, "constant upload failed"));
     p.union_warps = hanf::union_occupancy_warps(s.W, c->nsm);
+    p.union_async_warps = hanf::union_async_warps(s.W, c->nsm);
+    p.warp_variant = (o.gather_variant == 2 && p.union_async_warps > 0) ? 2 : 1;
 
     rc = reset(c, s.history);
     if (rc) return bail(rc);
@@ -572,10 +611,22 @@ int hanf_registers(hanf_ctx *c, int32_t run, int64_t first, int64_t count, uint8
     if (count == 0) return HANF_OK;
     int rc = read_ctl(c);
     if (rc) return rc;
-    const uint8_t *src = c->plan.regs[c->host_ctl.parity] + first * c->plan.W + (int64_t)run * c->plan.m;
-    CU(cudaMemcpy2DAsync(out, c->plan.m, src, c->plan.W, c->plan.m, count, cudaMemcpyDeviceToHost,
-                         c->stream));
-    CU(cudaStreamSynchronize(c->stream));
+    const uint8_t *regs = c->plan.regs[c->host_ctl.parity];
+    const int W = c->plan.W, m = c->plan.m;
+    if (!c->perm) {
+        const uint8_t *src = regs + first * W + (int64_t)run * m;
+        CU(cudaMemcpy2DAsync(out, m, src, W, m, count, cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        return HANF_OK;
+    }
+    // relabelled storage: gather the rows into input order, chunk by chunk
+    for (int64_t i = 0; i < count; i += kStageRows) {
+        const int64_t k = std::min<int64_t>(kStageRows, count - i);
+        CU(hanf::launch_gather_rows(regs, c->perm, first + i, k, W, c->stage, c->stream));
+        CU(cudaMemcpy2DAsync(out + i * m, m, c->stage + (int64_t)run * m, W, m, k,
+                             cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
     return HANF_OK;
 }
 

@@ -28,12 +28,11 @@ struct DevCtl {
     int32_t bad_graph;   // set by the CSR validator
     int32_t pad_;
     int32_t T_run[kMaxRuns];                 // first pass that left run r unchanged
-    unsigned long long list_count[2];        // length of changed-node list [parity]
+    unsigned long long changed_count[2];     // nodes changed into regs[parity]
     unsigned long long run_changed[kMaxRuns];
     unsigned long long last_changed;         // nodes changed by the last pass
     unsigned long long cand_count[2];        // systolic candidates: small, medium degree
-    unsigned long long changed_in_arcs;      // sum of in-degrees of nodes changed this pass
-    unsigned long long last_changed_in_arcs; // same, for the last completed pass
+    unsigned long long changed_in_arcs;      // in-degree sum of the nodes the last pass changed
     // work counters since initialisation
     unsigned long long passes, push_passes, arcs_scanned, arcs_gathered, own_reads, writes;
 };
@@ -54,7 +53,6 @@ struct Plan {
     unsigned long long *cand;         // systolic candidates of the coming pass
     int32_t *cand_list[2];            // the candidates, small / medium degree (hubs: by bit)
     int32_t d_small, d_hub;           // degree class bounds
-    int32_t *list[2];                 // changed-node lists (parity-indexed)
     const int32_t *nodes;             // [small | medium | hub] node lists
     int64_t n_small, n_med, n_hub;
     const int32_t *seg_node;          // hub segments: node, arc range
@@ -70,9 +68,12 @@ struct Plan {
     const double *lc;                 // m+1 linear-counting values m ln(m/V)
     double amm;                       // alpha_m m^2
     const uint64_t *seeds;            // R run seeds
+    const int32_t *orig_id;           // input id of every stored node (null: identity)
     int32_t frontier, push_den, dense_den;
     int32_t history_cap;
     int32_t union_warps;              // resident warps of the union launch
+    int32_t union_async_warps;        // resident warps of the asynchronous-copy variant
+    int32_t warp_variant;             // medium/hub gathers: 1 register batches, 2 async copies
     DevCtl *ctl;
 };
 
@@ -83,6 +84,7 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
                         cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch);
 int union_occupancy_warps(int W, int nsm);
+int union_async_warps(int W, int nsm);
 
 // Preprocessing (create time).
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *tmp,
@@ -98,6 +100,16 @@ cudaError_t launch_hub_segments(const Plan &p, int32_t d_hub, int64_t *seg_count
 cudaError_t launch_transpose(const Plan &p, int64_t *in_off, int32_t *in_src, int64_t *cursor,
                              int64_t *tmp, int64_t tmp_elems, cudaStream_t s);
 int64_t classify_blocks(int64_t n);
+
+// Node relabelling by in-degree class (create time) and the row gather that
+// maps stored rows back to input ids.
+cudaError_t launch_relabel(const int64_t *off, const int32_t *tgt, int64_t n, int64_t arcs,
+                           unsigned long long *indeg, int64_t *counts, int64_t *offs,
+                           int64_t *tmp, int64_t tmp_elems, int32_t *perm, int32_t *inv,
+                           int64_t *deg, int64_t *off2, int32_t *tgt2, cudaStream_t s);
+int64_t relabel_count_elems(int64_t n);
+cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
+                               int64_t count, int W, uint8_t *out, cudaStream_t s);
 
 // Store the calling thread's message for hanf_last_error().
 void record_error(const char *msg);

@@ -234,12 +234,14 @@ __device__ __forceinline__ void warp_gather(const int32_t *__restrict__ tgt, con
 template <int LANES, int VPL>
 __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Row<LANES, VPL> &acc,
                                                 bool need, bool inR, int32_t v, int gl,
-                                                uint32_t &c_own, uint32_t &c_write)
+                                                uint32_t &c_own, uint32_t &c_write,
+                                                const Row<LANES, VPL> *pre = nullptr)
 {
     Row<LANES, VPL> own, nw;
     uint32_t mask = 0;
     if (need) {
-        row_load(own, p.regs[cur], v, gl);
+        if (pre) own = *pre;
+        else row_load(own, p.regs[cur], v, gl);
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
             nw.v[k] = vmax4(acc.v[k], own.v[k]);
@@ -256,8 +258,9 @@ __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Ro
     return mask;
 }
 
-// Record the nodes whose counters changed: bitmap bit, compact list entry and
-// per-run counts.  Called by all lanes; `leader` marks one lane per node.
+// Record the nodes whose counters changed: bitmap bit, node count and
+// per-run counts, all with fire-and-forget reductions so that no warp waits
+// on them.  Called by all lanes; `leader` marks one lane per node.
 __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, int32_t v,
                                           uint32_t mask)
 {
@@ -265,25 +268,11 @@ __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, i
     const unsigned bal = __ballot_sync(kFull, ch);
     if (bal == 0) return;
     const int lane = threadIdx.x & 31;
-    const int first = __ffs(bal) - 1;
-    unsigned long long base = 0;
-    if (lane == first)
-        base = atomicAdd(&p.ctl->list_count[cur ^ 1], (unsigned long long)__popc(bal));
-    base = __shfl_sync(kFull, base, first);
-    if (ch) {
-        const int rank = __popc(bal & ((1u << lane) - 1u));
-        p.list[cur ^ 1][base + rank] = v;
-        atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
-    }
+    if (lane == 0) atomicAdd(&p.ctl->changed_count[cur ^ 1], (unsigned long long)__popc(bal));
+    if (ch) atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
     for (int r = 0; r < p.R; ++r) {
         const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u));
         if (lane == 0 && br) atomicAdd(&p.ctl->run_changed[r], (unsigned long long)__popc(br));
-    }
-    if (p.in_off) {
-        unsigned long long indeg = ch ? (unsigned long long)(__ldg(p.in_off + v + 1) - __ldg(p.in_off + v)) : 0ull;
-#pragma unroll
-        for (int s = 16; s; s >>= 1) indeg += __shfl_xor_sync(kFull, indeg, s);
-        if (lane == 0 && indeg) atomicAdd(&p.ctl->changed_in_arcs, indeg);
     }
 }
 
@@ -314,7 +303,7 @@ template <int LANES, int VPL>
 __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
 {
     constexpr int GPW = 32 / LANES;
-    constexpr int U = 8 / VPL;
+    constexpr int U = 4 / VPL > 0 ? 4 / VPL : 1;
     const DevCtl *ctl = p.ctl;
     if (ctl->done) return;
     const int cur = ctl->parity;
@@ -332,23 +321,40 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
     // systolic passes visit the small-degree candidates only
     const int32_t *list = push ? p.cand_list[0] : p.nodes;
     const int64_t count = push ? (int64_t)ctl->cand_count[0] : p.n_small;
-    for (int64_t base = warp * GPW; base < count; base += nwarps * GPW) {
-        const int64_t idx = base + g;
-        const bool valid = idx < count;
-        const int32_t v = valid ? __ldg(list + idx) : 0;
-        const bool take = valid;
+    // dense and systolic passes need almost every visited node's own counter:
+    // load it next to the gathers instead of after them
+    const bool own_early = !test || push;
+    const int64_t stride = nwarps * GPW;
+    // node ids two iterations ahead, arc ranges one iteration ahead
+    int64_t idx_ahead = warp * GPW + g;
+    int32_t v_next = idx_ahead < count ? __ldg(list + idx_ahead) : -1;
+    int64_t beg_next = v_next >= 0 ? __ldg(p.off + v_next) : 0;
+    int64_t end_next = v_next >= 0 ? __ldg(p.off + v_next + 1) : 0;
+    idx_ahead += stride;
+    int32_t v_after = idx_ahead < count ? __ldg(list + idx_ahead) : -1;
+    for (int64_t base = warp * GPW; base < count; base += stride) {
+        const int32_t v = v_next;
+        const int64_t beg = beg_next, end = end_next;
+        const bool valid = v >= 0;
+        v_next = v_after;
+        beg_next = v_next >= 0 ? __ldg(p.off + v_next) : 0;
+        end_next = v_next >= 0 ? __ldg(p.off + v_next + 1) : 0;
+        idx_ahead += stride;
+        v_after = idx_ahead < count ? __ldg(list + idx_ahead) : -1;
+        Row<LANES, VPL> own;
+        if (valid && own_early) row_load(own, rc, v, gl);
         Row<LANES, VPL> acc;
         row_zero(acc);
         bool any = false;
-        if (take) {
-            const int64_t beg = __ldg(p.off + v), end = __ldg(p.off + v + 1);
+        if (valid) {
             group_gather<LANES, VPL, U>(p.tgt, rc, Fc, test, beg, end, gl, gmask, gbase, acc, any,
                                         c_gather);
             if (gl == 0) c_scan += (uint32_t)(end - beg);
         }
-        const bool inR = take && !first && test_bit(Fc, v);
-        const bool need = take && (any || inR);
-        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+        const bool inR = valid && !first && test_bit(Fc, v);
+        const bool need = valid && (any || inR);
+        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write,
+                                          own_early ? &own : nullptr);
         warp_mark(p, cur, gl == 0 && valid, v, mask);
     }
     flush_counters(p, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
@@ -402,6 +408,179 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_warp(Plan p)
             warp_mark(p, cur, lane == 0, v, mask);
         }
     }
+    flush_counters(p, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
+}
+
+// ---------------------------------------------------------------- asynchronous gathers
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, bool valid)
+{
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const int n = valid ? 16 : 0;   // 0: nothing is read, the 16 bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gsrc), "r"(n)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Pipeline depth (stages of 32 arcs in the shared-memory ring of a warp).
+template <int LANES>
+struct AsyncCfg {
+    static constexpr int W = 16 * LANES;
+    static constexpr int D = W <= 64 ? 4 : 2;
+    static constexpr size_t smem_per_warp = (size_t)D * 32 * W;
+    static constexpr size_t smem_per_block = smem_per_warp * (kBlock / 32);
+};
+
+// Per-stage bookkeeping kept in shared memory next to the ring.
+struct StageMeta {
+    int64_t item;   // work item the stage belongs to, -1 if empty
+    int32_t valid;  // rows actually gathered
+    int32_t last;   // 1 if it is the item's last stage
+};
+
+// Union pass over medium nodes and hub segments with the row gathers in
+// flight as asynchronous copies: every warp streams its work items as stages
+// of up to 32 arcs; the targets of a stage are loaded one stage ahead, the
+// rows of D-1 stages are in flight while the oldest is merged from shared
+// memory.  Rows of skipped successors are zero-filled, the identity of max.
+// For rows of at most 128 bytes (LANES <= 8, one vector per lane).
+template <int LANES>
+__global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
+{
+    using Cfg = AsyncCfg<LANES>;
+    constexpr int GPW = 32 / LANES;
+    constexpr int D = Cfg::D;
+    static_assert(GPW * LANES == 32, "lane groups tile the warp");
+    extern __shared__ uint4 smem_raw[];
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const bool test = ctl->mode != kModeDense;
+    const bool push = ctl->mode == kModePush;
+    const uint8_t *rc = p.regs[cur];
+    const unsigned long long *Fc = p.F[cur];
+    const int32_t *med = push ? p.cand_list[1] : p.nodes + p.n_small;
+    const int64_t total = p.n_seg + (push ? (int64_t)ctl->cand_count[1] : p.n_med);
+    const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
+    const int wib = threadIdx.x >> 5;
+    uint4 *ring = smem_raw + (size_t)wib * (Cfg::smem_per_warp / 16);
+    StageMeta *meta = reinterpret_cast<StageMeta *>(smem_raw + (Cfg::smem_per_block / 16)) + wib * D;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+
+    // ---- producer state (warp-uniform) ----
+    int64_t p_it = warp - nwarps, p_e = 0, p_end = 0;
+    auto next_item = [&]() {
+        // advance to the next item that has arcs to merge; untaken hub
+        // segments (systolic pass, hub not a candidate) just publish "nothing"
+        for (;;) {
+            p_it += nwarps;
+            if (p_it >= total) return;
+            if (p_it < p.n_seg) {
+                const int32_t v = __ldg(p.seg_node + p_it);
+                if (push && !test_bit(p.cand, v)) {
+                    if (lane == 0) p.hub_any[p_it] = 0;
+                    continue;
+                }
+                p_e = __ldg(p.seg_beg + p_it);
+                p_end = __ldg(p.seg_end + p_it);
+            } else {
+                const int32_t v = __ldg(med + (p_it - p.n_seg));
+                p_e = __ldg(p.off + v);
+                p_end = __ldg(p.off + v + 1);
+            }
+            if (lane == 0) c_scan += (uint32_t)(p_end - p_e);
+            return;
+        }
+    };
+    next_item();
+    // targets of the next stage to issue, loaded one stage ahead
+    int32_t t_next = (p_it < total && p_e + lane < p_end) ? __ldg(p.tgt + p_e + lane) : -1;
+
+    auto produce = [&](int slot) {
+        uint4 *buf = ring + (size_t)slot * 32 * LANES;
+        if (p_it >= total) {
+            if (lane == 0) meta[slot].item = -1;
+            cp_async_commit();
+            return;
+        }
+        int32_t w = t_next;
+        const int64_t it = p_it;
+        const bool last = p_e + 32 >= p_end;
+        // advance the producer and prefetch the following stage's targets
+        p_e += 32;
+        if (last) next_item();
+        t_next = (p_it < total && p_e + lane < p_end) ? __ldg(p.tgt + p_e + lane) : -1;
+        if (w >= 0 && test && !test_bit(Fc, w)) w = -1;
+        const unsigned live = __ballot_sync(kFull, w >= 0);
+        // lane (g, gl) copies the gl-th 16 bytes of rows g, g+GPW, ...
+#pragma unroll
+        for (int k = 0; k < LANES; ++k) {
+            const int r = g + GPW * k;
+            const int32_t wr = __shfl_sync(kFull, w, r);
+            const uint8_t *src = wr >= 0 ? rc + (int64_t)wr * Cfg::W + gl * 16 : rc;
+            cp_async16(buf + r * LANES + gl, src, wr >= 0);
+        }
+        cp_async_commit();
+        if (lane == 0) {
+            meta[slot].item = it;
+            meta[slot].valid = __popc(live);
+            meta[slot].last = last ? 1 : 0;
+        }
+    };
+
+    Row<LANES, 1> acc;
+    row_zero(acc);
+    bool any = false;
+    auto consume = [&](int slot) -> bool {
+        cp_async_wait<D - 1>();
+        __syncwarp();
+        const StageMeta m = meta[slot];
+        if (m.item < 0) {
+            __syncwarp();
+            return false;
+        }
+        const uint4 *buf = ring + (size_t)slot * 32 * LANES;
+#pragma unroll
+        for (int k = 0; k < LANES; ++k) acc.v[0] = vmax4(acc.v[0], buf[(g + GPW * k) * LANES + gl]);
+        if (m.valid) any = true;
+        c_gather += m.valid;
+        __syncwarp();
+        if (m.last) {
+            row_warp_max(acc);
+            const bool anyw = any;   // warp-uniform: every lane saw the same stages
+            if (m.item < p.n_seg) {
+                if (g == 0) row_store(p.hub_part, m.item, acc, gl);
+                if (lane == 0) p.hub_any[m.item] = anyw ? 1 : 0;
+            } else {
+                const int32_t v = __ldg(med + (m.item - p.n_seg));
+                const bool inR = !first && test_bit(Fc, v);
+                const bool need = (anyw || inR) && g == 0;
+                const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+                warp_mark(p, cur, lane == 0, v, mask);
+            }
+            row_zero(acc);
+            any = false;
+        }
+        return true;
+    };
+
+#pragma unroll
+    for (int s = 0; s < D - 1; ++s) produce(s);
+    for (int k = 0;; ++k) {
+        produce((k + D - 1) % D);
+        if (!consume(k % D) && p_it >= total) break;
+    }
+    cp_async_wait<0>();
     flush_counters(p, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
 }
 
@@ -463,14 +642,14 @@ __global__ void k_prep(Plan p)
     else if (p.frontier == HANF_FRONTIER_AUTO && p.in_off != nullptr && changed * p.push_den < p.n)
         mode = kModePush;
     else if (p.in_off != nullptr
-                 ? (long long)c->last_changed_in_arcs * p.dense_den >= p.arcs
+                 ? (long long)c->changed_in_arcs * p.dense_den >= p.arcs
                  : changed * p.dense_den >= p.n)
         mode = kModeDense;   // most successors changed: skip the per-arc test
     c->mode = mode;
-    c->list_count[c->parity ^ 1] = 0;
+    c->changed_count[c->parity ^ 1] = 0;
     c->cand_count[0] = 0;
     c->cand_count[1] = 0;
-    c->changed_in_arcs = 0;
+    c->changed_in_arcs = 0;     // the estimator sums it again after this pass
     for (int r = 0; r < kMaxRuns; ++r) c->run_changed[r] = 0;
 }
 
@@ -516,25 +695,27 @@ __global__ void k_mark(Plan p)
 {
     const DevCtl *c = p.ctl;
     if (c->done || c->mode != kModePush) return;
-    const int cur = c->parity;
-    const int64_t cnt = (int64_t)c->list_count[cur];
-    const int32_t *lst = p.list[cur];
+    const unsigned long long *Fc = p.F[c->parity];
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < cnt; i += nwarps) {
-        const int32_t w = lst[i];
-        const int64_t beg = p.in_off[w], deg = p.in_off[w + 1] - beg;
-        // item 0 is w itself, item j >= 1 its (j-1)-th predecessor
-        for (int64_t j0 = 0; j0 <= deg; j0 += 32) {
-            const int64_t j = j0 + lane;
-            const int32_t u = j == 0 ? w : (j <= deg ? __ldg(p.in_src + beg + j - 1) : -1);
-            bool fresh = false;
-            if (u >= 0) {
-                const unsigned long long bit = 1ull << (u & 63);
-                fresh = (atomicOr(&p.cand[u >> 6], bit) & bit) == 0ull;
+    for (int64_t i = warp; i < p.nwords; i += nwarps) {
+        unsigned long long bits = Fc[i];
+        while (bits) {
+            const int32_t w = (int32_t)(i * 64 + (__ffsll((long long)bits) - 1));
+            bits &= bits - 1;
+            const int64_t beg = p.in_off[w], deg = p.in_off[w + 1] - beg;
+            // item 0 is w itself, item j >= 1 its (j-1)-th predecessor
+            for (int64_t j0 = 0; j0 <= deg; j0 += 32) {
+                const int64_t j = j0 + lane;
+                const int32_t u = j == 0 ? w : (j <= deg ? __ldg(p.in_src + beg + j - 1) : -1);
+                bool fresh = false;
+                if (u >= 0) {
+                    const unsigned long long bit = 1ull << (u & 63);
+                    fresh = (atomicOr(&p.cand[u >> 6], bit) & bit) == 0ull;
+                }
+                cand_append(p, fresh, u);
             }
-            cand_append(p, fresh, u);
         }
     }
 }
@@ -547,9 +728,8 @@ __global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
     unsigned keep = 0;
     if (!c->done) {
         const int nxt = c->parity ^ 1;
-        const unsigned long long changed = c->list_count[nxt];
+        const unsigned long long changed = c->changed_count[nxt];
         c->last_changed = changed;
-        c->last_changed_in_arcs = c->changed_in_arcs;
         c->passes += 1;
         if (c->mode == kModePush) c->push_passes += 1;
         for (int r = 0; r < p.R; ++r)
@@ -606,7 +786,7 @@ __device__ __forceinline__ double node_size(const Plan &p, const uint8_t *rc, in
 // block's registers.
 __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
 {
-    const DevCtl *c = p.ctl;
+    DevCtl *c = p.ctl;
     if (c->done) return;
     const bool all = c->t == 0;
     const uint8_t *rc = p.regs[c->parity];
@@ -620,6 +800,17 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
         const int64_t blk = it - (int64_t)r * p.nwords;
         if (!all && Fc[blk] == 0ull) continue;
         const int64_t v0 = blk * 64 + lane, v1 = v0 + 32;
+        if (!all && r == 0 && p.in_off) {
+            // in-arcs of the nodes that changed: the share of arcs whose
+            // successor changed, which picks the next pass's flavour
+            const unsigned long long word = Fc[blk];
+            unsigned long long d = 0;
+            if ((word >> lane) & 1ull) d += (unsigned long long)(p.in_off[v0 + 1] - p.in_off[v0]);
+            if ((word >> (lane + 32)) & 1ull) d += (unsigned long long)(p.in_off[v1 + 1] - p.in_off[v1]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+            if (lane == 0 && d) atomicAdd(&p.ctl->changed_in_arcs, d);
+        }
         const double e0 = v0 < p.n ? node_size(p, rc, v0, r) : 0.0;
         const double e1 = v1 < p.n ? node_size(p, rc, v1, r) : 0.0;
         double s = e0 + e1;
@@ -684,7 +875,8 @@ __global__ void __launch_bounds__(kBlock) k_init(Plan p)
         const int byte0 = (int)(c - v * cpr) << 4;
         const int r = byte0 >> p.b;
         const int o = byte0 & (p.m - 1);
-        const uint64_t h = splitmix64((uint64_t)v ^ p.seeds[r]);
+        const uint64_t item = p.orig_id ? (uint64_t)__ldg(p.orig_id + v) : (uint64_t)v;
+        const uint64_t h = splitmix64(item ^ p.seeds[r]);
         const int idx = (int)(h >> (64 - p.b));
         const uint64_t rest = h << p.b;
         int rho = rest ? __clzll((long long)rest) + 1 : 64 - p.b + 1;
@@ -893,6 +1085,96 @@ __global__ void k_transpose_fill(Plan p, const int64_t *in_off, unsigned long lo
     }
 }
 
+// ---------------------------------------------------------------- relabelling
+
+// Popularity class of a node: 0 for the largest in-degrees, 31 for none.
+// Nodes are stored hottest class first, so the counters most often gathered
+// share cache lines and DRAM pages.
+constexpr int kHotClasses = 32;
+
+__device__ __forceinline__ int hot_class(unsigned long long indeg)
+{
+    return 31 - (63 - __clzll((long long)(indeg + 1)));
+}
+
+// counts[c * ntiles + tile] = nodes of class c in the tile.
+__global__ void __launch_bounds__(kBlock) k_hot_count(const unsigned long long *indeg, int64_t n,
+                                                      int64_t *counts, int64_t ntiles)
+{
+    __shared__ int hist[kHotClasses];
+    if (threadIdx.x < kHotClasses) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t v0 = (int64_t)blockIdx.x * kClassTile + (int64_t)threadIdx.x * kClassPerThread;
+    for (int k = 0; k < kClassPerThread; ++k)
+        if (v0 + k < n) atomicAdd(&hist[hot_class(indeg[v0 + k])], 1);
+    __syncthreads();
+    if (threadIdx.x < kHotClasses) counts[threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
+}
+
+// Stable scatter: new position of every node (class order, then id order).
+__global__ void __launch_bounds__(kBlock) k_hot_scatter(const unsigned long long *indeg, int64_t n,
+                                                        const int64_t *offs, int64_t ntiles,
+                                                        int32_t *perm, int32_t *inv)
+{
+    const int64_t v0 = (int64_t)blockIdx.x * kClassTile + (int64_t)threadIdx.x * kClassPerThread;
+    int cls[kClassPerThread];
+    for (int k = 0; k < kClassPerThread; ++k) cls[k] = v0 + k < n ? hot_class(indeg[v0 + k]) : -1;
+    for (int c = 0; c < kHotClasses; ++c) {
+        int mine = 0;
+        for (int k = 0; k < kClassPerThread; ++k) mine += cls[k] == c;
+        int64_t pos = block_excl_scan(mine, nullptr) + offs[c * ntiles + blockIdx.x];
+        for (int k = 0; k < kClassPerThread; ++k)
+            if (cls[k] == c) {
+                perm[v0 + k] = (int32_t)pos;
+                inv[pos] = (int32_t)(v0 + k);
+                ++pos;
+            }
+    }
+}
+
+// Out-degree of every new node (input of the new offsets' scan).
+__global__ void k_new_degree(const int64_t *off, const int32_t *inv, int64_t n, int64_t *deg)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u <= n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        if (u == n) {
+            deg[u] = 0;
+        } else {
+            const int32_t v = inv[u];
+            deg[u] = off[v + 1] - off[v];
+        }
+    }
+}
+
+// Successor lists in the new numbering: a warp per new node.
+__global__ void k_relabel_fill(const int64_t *off, const int32_t *tgt, const int32_t *perm,
+                               const int32_t *inv, int64_t n, const int64_t *off2, int32_t *tgt2)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const int32_t v = inv[u];
+        const int64_t b = off[v], d = off[v + 1] - b, o = off2[u];
+        for (int64_t j = lane; j < d; j += 32) tgt2[o + j] = perm[__ldg(tgt + b + j)];
+    }
+}
+
+// Rows of nodes (original ids first..first+count) gathered into a staging
+// buffer in original order.
+__global__ void k_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t first, int64_t count,
+                              int W, uint8_t *out)
+{
+    const int64_t cpr = W >> 4;
+    const int64_t total = count * cpr;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = c / cpr, j = c - i * cpr;
+        const int64_t row = perm ? perm[first + i] : first + i;
+        reinterpret_cast<uint4 *>(out)[c] = reinterpret_cast<const uint4 *>(regs)[row * cpr + j];
+    }
+}
+
 int grid_for(int64_t work, int per_block, int64_t cap = 152 * 32)
 {
     int64_t g = (work + per_block - 1) / per_block;
@@ -908,7 +1190,18 @@ struct UnionKernels {
     static cudaError_t launch(const Plan &p, cudaStream_t s)
     {
         const int blocks = (p.union_warps * 32 + kBlock - 1) / kBlock;
-        k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+        if constexpr (VPL == 1 && LANES <= 8) {
+            if (p.warp_variant == 2) {
+                using Cfg = AsyncCfg<LANES>;
+                const size_t smem = Cfg::smem_per_block + sizeof(StageMeta) * Cfg::D * (kBlock / 32);
+                const int ablocks = (p.union_async_warps * 32 + kBlock - 1) / kBlock;
+                k_union_warp_async<LANES><<<ablocks, kBlock, smem, s>>>(p);
+            } else {
+                k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+            }
+        } else {
+            k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+        }
         k_union_small<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
         return cudaGetLastError();
     }
@@ -925,6 +1218,23 @@ struct UnionKernels {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_union_small<LANES, VPL>, kBlock, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_union_warp<LANES, VPL>, kBlock, 0);
         return a < b ? a : b;
+    }
+    // Resident blocks of the asynchronous-copy warp kernel (0 where it does
+    // not apply); also opts it in to more than 48 KB of shared memory.
+    static int async_occupancy()
+    {
+        if constexpr (VPL == 1 && LANES <= 8) {
+            using Cfg = AsyncCfg<LANES>;
+            const size_t smem = Cfg::smem_per_block + sizeof(StageMeta) * Cfg::D * (kBlock / 32);
+            cudaFuncSetAttribute(k_union_warp_async<LANES>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_union_warp_async<LANES>, kBlock,
+                                                          smem);
+            return nb;
+        } else {
+            return 0;
+        }
     }
 };
 
@@ -947,6 +1257,16 @@ cudaError_t with_width(int W, F &&f)
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+
+int union_async_warps(int W, int nsm)
+{
+    int nb = 0;
+    with_width(W, [&](auto k) {
+        nb = decltype(k)::async_occupancy();
+        return cudaSuccess;
+    });
+    return nb * nsm * (kBlock / 32);
+}
 
 int union_occupancy_warps(int W, int nsm)
 {
@@ -1082,6 +1402,43 @@ cudaError_t launch_transpose(const Plan &p, int64_t *in_off, int32_t *in_src, in
     k_transpose_fill<<<152 * 16, kBlock, 0, s>>>(p, in_off,
                                                  reinterpret_cast<unsigned long long *>(cursor),
                                                  in_src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relabel(const int64_t *off, const int32_t *tgt, int64_t n, int64_t arcs,
+                           unsigned long long *indeg, int64_t *counts, int64_t *offs,
+                           int64_t *tmp, int64_t tmp_elems, int32_t *perm, int32_t *inv,
+                           int64_t *deg, int64_t *off2, int32_t *tgt2, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    Plan q{};
+    q.n = n;
+    q.arcs = arcs;
+    q.off = off;
+    q.tgt = tgt;
+    cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * (n + 1), s);
+    k_in_degree<<<grid_for(arcs, kBlock, 152 * 64), kBlock, 0, s>>>(q, indeg);
+    const int64_t nt = classify_blocks(n);
+    k_hot_count<<<(unsigned)nt, kBlock, 0, s>>>(indeg, n, counts, nt);
+    cudaMemsetAsync(counts + kHotClasses * nt, 0, sizeof(int64_t), s);
+    cudaError_t err = scan_exclusive_i64(counts, offs, kHotClasses * nt + 1, tmp, tmp_elems, s);
+    if (err != cudaSuccess) return err;
+    k_hot_scatter<<<(unsigned)nt, kBlock, 0, s>>>(indeg, n, offs, nt, perm, inv);
+    k_new_degree<<<grid_for(n + 1, kBlock, 152 * 64), kBlock, 0, s>>>(off, inv, n, deg);
+    err = scan_exclusive_i64(deg, off2, n + 1, tmp, tmp_elems, s);
+    if (err != cudaSuccess) return err;
+    k_relabel_fill<<<152 * 32, kBlock, 0, s>>>(off, tgt, perm, inv, n, off2, tgt2);
+    return cudaGetLastError();
+}
+
+int64_t relabel_count_elems(int64_t n) { return kHotClasses * classify_blocks(n) + 1; }
+
+cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
+                               int64_t count, int W, uint8_t *out, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_gather_rows<<<grid_for(count * (W >> 4), kBlock, 152 * 32), kBlock, 0, s>>>(
+        regs, perm, first, count, W, out);
     return cudaGetLastError();
 }
 

@@ -184,3 +184,33 @@ def test_history_exhausted(H, oracle):
         np.testing.assert_allclose(N[0, :10], No[:10], rtol=RTOL)
         N2, T2 = h.run()                  # the context stays usable
         assert T2[0] == len(No) - 1
+
+
+@pytest.mark.parametrize("frontier", ["off", "auto"])
+def test_input_order_storage(H, oracle, frontier):
+    """relabel=False keeps counters in input order; results are identical."""
+    off, tgt = G.rmat(12, seed=6)
+    check_run(H, oracle, off, tgt, 6, frontier=frontier, relabel=False)
+    check_run(H, oracle, off, tgt, 6, R=4, frontier=frontier, relabel=False, use_graph=True)
+
+
+def test_relabelled_registers_by_input_id(H, oracle):
+    """Register reads of arbitrary id ranges map back to input ids."""
+    off, tgt = G.rmat(12, seed=9)
+    n = off.size - 1
+    with H.HyperANF(off, tgt, 6, SEED, runs=2) as h:
+        h.run()
+        full = [h.registers(r) for r in range(2)]
+        for first, count in [(0, 1), (17, 100), (n - 5, 5), (1000, 0)]:
+            for r in range(2):
+                assert np.array_equal(h.registers(r, first, count), full[r][first:first + count])
+
+
+@pytest.mark.parametrize("log2m", [4, 5, 6, 7, 8])
+def test_async_gather_variant(H, oracle, log2m):
+    """The asynchronous-copy gathers give the same results (rows up to 128 B;
+    wider rows fall back to register batches)."""
+    off, tgt = G.rmat(13, seed=10)
+    for frontier in ("pull", "auto"):
+        check_run(H, oracle, off, tgt, log2m, frontier=frontier, gather_variant=2,
+                  small_max_deg=4, hub_min_deg=256)
