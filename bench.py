@@ -244,7 +244,16 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
     ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--gather-ceiling", action="store_true",
+                    help="build and run the random 64-byte row gather probe, then exit")
     args = ap.parse_args()
+    if args.gather_ceiling:
+        src = os.path.join(ROOT, "paper_1011_5599_gb300", "probe", "gather_ceiling.cu")
+        exe = os.path.join(ROOT, "paper_1011_5599_gb300", "_lib", "gather_ceiling")
+        os.makedirs(os.path.dirname(exe), exist_ok=True)
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
+                        src], check=True)
+        return subprocess.run([exe]).returncode
     if args.impl == "reference":
         return run_reference(args)
 
