@@ -50,6 +50,8 @@ extern "C" {
 #define HANF_ECUDA (-3)      /* a CUDA runtime call failed                  */
 #define HANF_ERANGE (-4)     /* history capacity exhausted before stability */
 #define HANF_ESTATE (-5)     /* call not valid in the context's state       */
+#define HANF_ETIMEOUT (-6)   /* a wait ran out of time                       */
+#define HANF_ECANCELLED (-7) /* the job was cancelled before it started      */
 
 /* Frontier policy (Section 3.3, "tracking modified counters" and "systolic
  * computation"). */
@@ -178,6 +180,62 @@ HANF_API int hanf_stats(const double *N, int32_t T, double alpha, int32_t exclud
  * and must be serialised by the caller. */
 HANF_API int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2m, int32_t runs,
                                   double *N_out, void *stream);
+
+/* ---- Serving: continuous batching of HyperANF jobs --------------------------
+ * A server owns worker threads, each with its own CUDA stream, and a device
+ * arena the caller reserved (the HBM budget).  Jobs are admitted in arrival
+ * order as soon as a worker is free and the job's workspace (as sized by
+ * hanf_workspace_size) fits in the arena; the admitted job runs the whole of
+ * Algorithm 2 as one CUDA graph on its worker's stream, so jobs of different
+ * workers overlap on the GPU.  Every job has its own context: its result is
+ * the same whether it runs alone or among others.  (The paper runs one graph
+ * at a time; this layer is the serving pattern around its Algorithm 2.) */
+typedef struct hanf_server hanf_server;
+
+typedef struct hanf_job {
+    int64_t n, arcs;          /* graph size                                       */
+    const int64_t *offsets;   /* CSR as for hanf_create; the memory must stay
+                                 valid until hanf_server_wait returns for the job */
+    const int32_t *targets;
+    int32_t graph_on_device;  /* 0: host pointers (copied at admission), 1: device */
+    int32_t log2m;            /* 4..8                                               */
+    int32_t runs;             /* R, as for hanf_opts.runs                          */
+    int32_t max_iter;         /* passes allowed; 0 = 4096                          */
+    uint64_t seed;            /* run seeds splitmix64(seed + r)                    */
+} hanf_job;
+
+/* Create a server over `arena` (device, 256-byte aligned, arena_bytes long,
+ * owned by the caller until hanf_server_destroy) with `workers` worker
+ * threads (1..64).  `base` gives the options every job uses (frontier, degree
+ * thresholds, relabelling; runs, streams, seeds and drivers are per job);
+ * NULL = defaults. */
+HANF_API int hanf_server_create(hanf_server **out, void *arena, size_t arena_bytes,
+                                int32_t workers, const hanf_opts *base);
+
+/* Queue a job; *id_out identifies it.  HANF_ENOMEM if the job cannot fit even
+ * in the empty arena. */
+HANF_API int hanf_server_submit(hanf_server *s, const hanf_job *job, uint64_t *id_out);
+
+/* Wait for a job (timeout_ms < 0: no limit; HANF_ETIMEOUT when it runs out, the
+ * job stays queued or running).  On success N_out (host, runs x cap, nullable)
+ * gets N_r(0..T) with T the job's last pass (entries after T_r repeat
+ * N_r(T_r)), T_out (runs, nullable) the T_r, and info_out (5 doubles,
+ * nullable) {latency ms from submission to completion, ms queued, ms on a
+ * worker, T, workspace bytes}.  The job's own failure code is returned as is.
+ * Each job can be waited for once. */
+HANF_API int hanf_server_wait(hanf_server *s, uint64_t id, int32_t timeout_ms, double *N_out,
+                              int32_t cap, int32_t *T_out, double *info_out);
+
+/* Cancel a job that has not started (HANF_ESTATE if it has). */
+HANF_API int hanf_server_cancel(hanf_server *s, uint64_t id);
+
+/* out = {jobs queued, jobs running, completed, failed, largest free arena
+ * block, arena bytes}; nout <= 6. */
+HANF_API int hanf_server_stats(hanf_server *s, double *out, int32_t nout);
+
+/* Stop the workers after their current jobs (queued jobs are cancelled) and
+ * free the server.  No other call on the server may be in progress. */
+HANF_API void hanf_server_destroy(hanf_server *s);
 
 /* Release the context (not the workspace, which belongs to the caller). */
 HANF_API void hanf_destroy(hanf_ctx *ctx);

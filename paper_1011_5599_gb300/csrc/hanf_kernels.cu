@@ -14,6 +14,8 @@
 // counters): the changed set is a bitmap F[p] of n bits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "hanf_internal.cuh"
 
 namespace hanf {
@@ -367,7 +369,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
 template <int LANES, int VPL>
 __global__ void __launch_bounds__(kBlock, 3) k_union_warp(Plan p)
 {
-    constexpr int GPW = 32 / LANES;
     const DevCtl *ctl = p.ctl;
     if (ctl->done) return;
     const int cur = ctl->parity;
@@ -1189,7 +1190,15 @@ template <int LANES, int VPL>
 struct UnionKernels {
     static cudaError_t launch(const Plan &p, cudaStream_t s)
     {
-        const int blocks = (p.union_warps * 32 + kBlock - 1) / kBlock;
+        // persistent grids, but no larger than the work: small graphs launch
+        // (and retire) only the blocks they can use
+        constexpr int GPW = 32 / LANES;
+        constexpr int WPB = kBlock / 32;
+        const int64_t persistent = (p.union_warps * 32 + kBlock - 1) / kBlock;
+        const int64_t warp_items = p.n_seg + p.n_med;
+        const int64_t small_items = (p.n_small + GPW - 1) / GPW;
+        const int blocks = (int)std::max<int64_t>(1, std::min(persistent, (warp_items + WPB - 1) / WPB));
+        const int sblocks = (int)std::max<int64_t>(1, std::min(persistent, (small_items + WPB - 1) / WPB));
         if constexpr (VPL == 1 && LANES <= 8) {
             if (p.warp_variant == 2) {
                 using Cfg = AsyncCfg<LANES>;
@@ -1202,7 +1211,7 @@ struct UnionKernels {
         } else {
             k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
         }
-        k_union_small<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
+        k_union_small<LANES, VPL><<<sblocks, kBlock, 0, s>>>(p);
         return cudaGetLastError();
     }
     static cudaError_t launch_hub(const Plan &p, cudaStream_t s)
@@ -1305,7 +1314,7 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
 {
     k_prep<<<1, 1, 0, s>>>(p);
     k_clear<<<grid_for(p.nwords, kBlock, 152 * 16), kBlock, 0, s>>>(p);
-    if (p.in_off) k_mark<<<152 * 8, kBlock, 0, s>>>(p);
+    if (p.in_off) k_mark<<<grid_for(p.nwords, kBlock / 32, 152 * 8), kBlock, 0, s>>>(p);
     if (ev0) cudaEventRecord(ev0, s);
     cudaError_t err = with_width(p.W, [&](auto k) { return decltype(k)::launch(p, s); });
     if (err != cudaSuccess) return err;

@@ -282,6 +282,38 @@ def job_stream(count: int = 2000, seed: int = 7, rate_per_s: float = 100.0,
     return jobs
 
 
+def er_torch(n: int, arcs: int, seed: int = 1, device: str = "cpu"):
+    """Directed ER on any torch device: `arcs` uniform draws, loops and
+    duplicates removed (so slightly fewer arcs)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    s = torch.randint(0, n, (arcs,), generator=g, device=device, dtype=torch.int64)
+    d = torch.randint(0, n, (arcs,), generator=g, device=device, dtype=torch.int64)
+    keep = s != d
+    keys = torch.unique(s[keep] * n + d[keep])
+    counts = torch.bincount(keys // n, minlength=n)
+    off = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=off[1:])
+    return off, (keys % n).to(torch.int32)
+
+
+def job_graph_torch(job: dict, device: str = "cuda"):
+    """The graph of one job descriptor as device tensors."""
+    import torch
+
+    n, kind = job["n"], job["kind"]
+    if kind == "er":
+        return er_torch(n, int(n * job["deg"]), seed=job["seed"], device=device)
+    if kind == "rmat":
+        scale = max(4, int(round(math.log2(n))))
+        return rmat(scale, edge_factor=max(1, int(round(job["deg"]))), seed=job["seed"],
+                    device=device, as_numpy=False)
+    off, tgt = grid2d(max(2, int(round(math.sqrt(n)))))
+    return torch.from_numpy(off).to(device), torch.from_numpy(tgt).to(device)
+
+
 def job_graph(job: dict):
     """The graph of one job descriptor (CSR on the host)."""
     n, kind = job["n"], job["kind"]

@@ -17,12 +17,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libhanf.so")
 
 HANF_OK, HANF_EINVAL, HANF_ENOMEM, HANF_ECUDA, HANF_ERANGE, HANF_ESTATE = 0, -1, -2, -3, -4, -5
+HANF_ETIMEOUT, HANF_ECANCELLED = -6, -7
 FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 
 # Every function declared in include/hanf.h.
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
            "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
-           "hanf_trace", "hanf_stats", "hanf_estimate_static", "hanf_destroy", "hanf_last_error")
+           "hanf_trace", "hanf_stats", "hanf_estimate_static", "hanf_server_create",
+           "hanf_server_submit", "hanf_server_wait", "hanf_server_cancel", "hanf_server_stats",
+           "hanf_server_destroy", "hanf_destroy", "hanf_last_error")
 TRACE_NAMES = ("t", "mode", "changed", "union_ms", "arcs_scanned", "arcs_gathered", "own_reads",
                "writes")
 
@@ -34,6 +37,14 @@ class HanfError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"hanf error {code}: {msg}")
         self.code = code
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("arcs", ctypes.c_int64),
+                ("offsets", ctypes.c_void_p), ("targets", ctypes.c_void_p),
+                ("graph_on_device", ctypes.c_int32), ("log2m", ctypes.c_int32),
+                ("runs", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class Opts(ctypes.Structure):
@@ -88,6 +99,20 @@ def lib():
         L.hanf_stats.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _i32, ctypes.POINTER(_f64)]
         L.hanf_estimate_static.restype = _i32
         L.hanf_estimate_static.argtypes = [_vp, _i64, _i32, _i32, _vp, _vp]
+        L.hanf_server_create.restype = _i32
+        L.hanf_server_create.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_size_t, _i32,
+                                         ctypes.POINTER(Opts)]
+        L.hanf_server_submit.restype = _i32
+        L.hanf_server_submit.argtypes = [_vp, ctypes.POINTER(Job), ctypes.POINTER(_u64)]
+        L.hanf_server_wait.restype = _i32
+        L.hanf_server_wait.argtypes = [_vp, _u64, _i32, ctypes.POINTER(_f64), _i32,
+                                       ctypes.POINTER(_i32), ctypes.POINTER(_f64)]
+        L.hanf_server_cancel.restype = _i32
+        L.hanf_server_cancel.argtypes = [_vp, _u64]
+        L.hanf_server_stats.restype = _i32
+        L.hanf_server_stats.argtypes = [_vp, ctypes.POINTER(_f64), _i32]
+        L.hanf_server_destroy.restype = None
+        L.hanf_server_destroy.argtypes = [_vp]
         L.hanf_destroy.restype = None
         L.hanf_destroy.argtypes = [_vp]
         L.hanf_last_error.restype = ctypes.c_char_p
@@ -277,3 +302,86 @@ class HyperANF:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Server:
+    """Continuous-batching HyperANF server (hanf_server_*): jobs are admitted
+    in arrival order into a device arena of ``arena_bytes`` (the HBM budget)
+    and run on ``workers`` concurrent streams."""
+
+    INFO = ("latency_ms", "queued_ms", "run_ms", "T", "workspace_bytes")
+
+    def __init__(self, arena_bytes: int, workers: int = 4, device=None, **opts):
+        import torch
+
+        self.device = torch.device(device if device is not None else "cuda")
+        self._opts, self._keep = make_opts(**opts)
+        self._arena = torch.empty(arena_bytes, dtype=torch.uint8, device=self.device)
+        self._jobs = {}
+        srv = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().hanf_server_create(ctypes.byref(srv), self._arena.data_ptr(), arena_bytes,
+                                           workers, ctypes.byref(self._opts)))
+        self._srv = srv
+
+    def submit(self, offsets, targets, log2m: int, seed: int, runs: int = 1,
+               max_iter: int = 0) -> int:
+        import torch
+
+        on_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
+        if on_dev:
+            off, tgt = offsets.to(torch.int64).contiguous(), targets.to(torch.int32).contiguous()
+            op, tp = off.data_ptr(), tgt.data_ptr()
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+            tgt = np.ascontiguousarray(targets, dtype=np.int32)
+            op, tp = off.ctypes.data, (tgt.ctypes.data if tgt.size else None)
+        n = (off.numel() if on_dev else off.size) - 1
+        arcs = tgt.numel() if on_dev else tgt.size
+        job = Job(n, arcs, op, tp, int(on_dev), log2m, runs, max_iter, seed & (2**64 - 1))
+        jid = _u64()
+        check(lib().hanf_server_submit(self._srv, ctypes.byref(job), ctypes.byref(jid)))
+        self._jobs[jid.value] = (off, tgt, runs)     # keep the graph alive until waited
+        return jid.value
+
+    def wait(self, jid: int, timeout_ms: int = -1, cap: int = 4097):
+        """Returns (list of N_r(0..T_r), array of T_r, info dict)."""
+        runs = self._jobs[jid][2]
+        N = np.zeros((runs, cap), dtype=np.float64)
+        T = np.zeros(runs, dtype=np.int32)
+        info = np.zeros(len(self.INFO), dtype=np.float64)
+        rc = lib().hanf_server_wait(self._srv, jid, timeout_ms,
+                                    N.ctypes.data_as(ctypes.POINTER(_f64)), cap,
+                                    T.ctypes.data_as(ctypes.POINTER(_i32)),
+                                    info.ctypes.data_as(ctypes.POINTER(_f64)))
+        if rc != HANF_ETIMEOUT:
+            self._jobs.pop(jid, None)
+        check(rc)
+        return [N[r, :T[r] + 1].copy() for r in range(runs)], T, dict(zip(self.INFO, info.tolist()))
+
+    def cancel(self, jid: int):
+        check(lib().hanf_server_cancel(self._srv, jid))
+
+    def stats(self) -> dict:
+        out = np.zeros(6, dtype=np.float64)
+        check(lib().hanf_server_stats(self._srv, out.ctypes.data_as(ctypes.POINTER(_f64)), 6))
+        return dict(zip(("queued", "running", "completed", "failed", "largest_free",
+                         "arena_bytes"), out.tolist()))
+
+    def close(self):
+        if getattr(self, "_srv", None):
+            lib().hanf_server_destroy(self._srv)
+            self._srv = None
+            self._arena = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
