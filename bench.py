@@ -357,6 +357,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
     ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick degree split and gather variant with hanf_autotune first")
     ap.add_argument("--gather-ceiling", action="store_true",
                     help="build and run the random 64-byte row gather probe, then exit")
     args = ap.parse_args()
@@ -403,9 +405,18 @@ def main():
     n, arcs = off.numel() - 1, tgt.numel()
     stream = torch.cuda.current_stream(device)
 
+    tuned = {"gather_variant": args.gather_variant}
+    tune_ms = None
+    if args.autotune:
+        from paper_1011_5599_gb300.hanf import autotune
+        cache = os.path.join(ROOT, "paper_1011_5599_gb300", "_lib", "tune_cache.txt")
+        t_tune = time.perf_counter()
+        tuned, tune_ms = autotune(off, tgt, log2m, 0x5EED, cache_path=cache, device=device,
+                                  runs=R, frontier="auto")
+        print(json.dumps({"autotune": tuned, "best_ms": tune_ms,
+                          "tuning_s": time.perf_counter() - t_tune}), file=sys.stderr)
     h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
-                 use_graph=args.driver == "graph", profile=args.driver == "host",
-                 gather_variant=args.gather_variant)
+                 use_graph=args.driver == "graph", profile=args.driver == "host", **tuned)
     for _ in range(args.warmup):
         h.run()
 
@@ -519,7 +530,7 @@ def main():
             "config": {"workload": wl["text"], "n": n, "arcs": arcs, "m": m, "runs": R,
                        "layout": "byte", "frontier": "auto", "driver": args.driver,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                       "l2": "inputs larger than L2 (no flush)",
+                       "l2": "inputs larger than L2 (no flush)", "tuned": tuned,
                        "graph_gen_s": round(t_gen, 2)},
             "T": T_list[-1], "passes_per_step": passes_list[-1],
             "gathered_rate": gathered / elapsed if elapsed else None,

@@ -66,9 +66,9 @@ typedef struct hanf_opts {
     int32_t runs;          /* R >= 1 independent seeded runs batched together  */
     int32_t frontier;      /* HANF_FRONTIER_*; default AUTO                    */
     int32_t push_den;      /* systolic switch below n/push_den changes; 4      */
-    int32_t small_max_deg; /* degree <= this: a lane group per node; 0 = auto  */
+    int32_t small_max_deg; /* degree <= this: a lane group per node; 0 = 256   */
     int32_t hub_min_deg;   /* degree > this: split in segments of this many
-                              arcs, a warp each; 0 = auto                      */
+                              arcs, a warp each; 0 = 16384                     */
     int32_t history_cap;   /* capacity of the device N(t) history; 0 = 4096    */
     int32_t use_graph;     /* hanf_run: 1 = whole loop as one CUDA graph with a
                               device-side while node (no host syncs)           */
@@ -180,6 +180,24 @@ HANF_API int hanf_stats(const double *N, int32_t T, double alpha, int32_t exclud
  * and must be serialised by the caller. */
 HANF_API int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2m, int32_t runs,
                                   double *N_out, void *stream);
+
+/* Autotuner (the paper has no counterpart; its thread pool needs no tuning):
+ * times candidate launch parameters of the union pass on this graph -- the
+ * degree split small_max_deg in {32,128,256,1024,4096}, hub_min_deg in
+ * {4096,16384,65536} and gather_variant in {1,2} -- each with its own
+ * context in `workspace`,
+ * one warm-up and one timed run of Algorithm 2, and returns the fastest in
+ * *best_out (the other fields copied from *base, NULL = defaults) and its
+ * time in *best_ms_out (nullable).  cache_path (nullable) names a text file:
+ * a result already stored for the same GPU, row width, graph size, frontier
+ * policy and relabelling is returned without timing; new results are
+ * appended.  Candidates whose workspace does not fit are skipped (size the
+ * workspace with hub_min_deg = 4096 to try them all).  Synchronises. */
+HANF_API int hanf_autotune(int64_t n, int64_t arcs, const int64_t *offsets,
+                           const int32_t *targets, int32_t graph_on_device, int32_t log2m,
+                           uint64_t seed, const hanf_opts *base, void *workspace,
+                           size_t workspace_bytes, const char *cache_path, hanf_opts *best_out,
+                           double *best_ms_out);
 
 /* ---- Serving: continuous batching of HyperANF jobs --------------------------
  * A server owns worker threads, each with its own CUDA stream, and a device

@@ -45,8 +45,8 @@ int fail(int code, const char *fmt, ...)
             return fail(HANF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
     } while (0)
 
-constexpr int32_t kDefaultSmall = 32;
-constexpr int32_t kDefaultHub = 1024;
+constexpr int32_t kDefaultSmall = 256;    // hanf_autotune's choice on R-MAT scale 27 and 24
+constexpr int32_t kDefaultHub = 16384;
 constexpr int32_t kDefaultHistory = 4096;
 constexpr int64_t kStageRows = 65536;   // rows per chunk of a relabelled register read
 

@@ -23,7 +23,8 @@ FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 # Every function declared in include/hanf.h.
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
            "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
-           "hanf_trace", "hanf_stats", "hanf_estimate_static", "hanf_server_create",
+           "hanf_trace", "hanf_stats", "hanf_estimate_static", "hanf_autotune",
+           "hanf_server_create",
            "hanf_server_submit", "hanf_server_wait", "hanf_server_cancel", "hanf_server_stats",
            "hanf_server_destroy", "hanf_destroy", "hanf_last_error")
 TRACE_NAMES = ("t", "mode", "changed", "union_ms", "arcs_scanned", "arcs_gathered", "own_reads",
@@ -99,6 +100,10 @@ def lib():
         L.hanf_stats.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _i32, ctypes.POINTER(_f64)]
         L.hanf_estimate_static.restype = _i32
         L.hanf_estimate_static.argtypes = [_vp, _i64, _i32, _i32, _vp, _vp]
+        L.hanf_autotune.restype = _i32
+        L.hanf_autotune.argtypes = [_i64, _i64, _vp, _vp, _i32, _i32, _u64, ctypes.POINTER(Opts),
+                                    _vp, ctypes.c_size_t, ctypes.c_char_p, ctypes.POINTER(Opts),
+                                    ctypes.POINTER(_f64)]
         L.hanf_server_create.restype = _i32
         L.hanf_server_create.argtypes = [ctypes.POINTER(_vp), _vp, ctypes.c_size_t, _i32,
                                          ctypes.POINTER(Opts)]
@@ -302,6 +307,36 @@ class HyperANF:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def autotune(offsets, targets, log2m: int, seed: int = 0x5EED, cache_path=None, device=None,
+             **opts) -> tuple[dict, float]:
+    """hanf_autotune on a graph; returns ({small_max_deg, hub_min_deg,
+    gather_variant}, best ms).  ``offsets``/``targets`` as for HyperANF."""
+    import torch
+
+    device = torch.device(device if device is not None else "cuda")
+    on_dev = isinstance(offsets, torch.Tensor) and offsets.is_cuda
+    if on_dev:
+        off, tgt = offsets.to(torch.int64).contiguous(), targets.to(torch.int32).contiguous()
+        op, tp, n, arcs = off.data_ptr(), tgt.data_ptr(), off.numel() - 1, tgt.numel()
+    else:
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        tgt = np.ascontiguousarray(targets, dtype=np.int32)
+        op, tp, n, arcs = off.ctypes.data, (tgt.ctypes.data if tgt.size else None), off.size - 1, tgt.size
+    stream = torch.cuda.current_stream(device)
+    base, keep = make_opts(stream=stream.cuda_stream, **opts)
+    widest, _ = make_opts(hub_min_deg=4096, small_max_deg=32, gather_variant=1, **opts)
+    size = workspace_size(n, arcs, log2m, widest, not on_dev)
+    ws = torch.empty(size, dtype=torch.uint8, device=device)
+    best = Opts()
+    ms = _f64()
+    path = None if cache_path is None else str(cache_path).encode()
+    check(lib().hanf_autotune(n, arcs, op, tp, int(on_dev), log2m, seed & (2**64 - 1),
+                              ctypes.byref(base), ws.data_ptr(), size, path, ctypes.byref(best),
+                              ctypes.byref(ms)))
+    return ({"small_max_deg": best.small_max_deg, "hub_min_deg": best.hub_min_deg,
+             "gather_variant": best.gather_variant}, ms.value)
 
 
 class Server:

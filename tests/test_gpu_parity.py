@@ -91,7 +91,8 @@ def test_degree_classes(H, oracle, small, hub):
 
 def test_rmat_hubs(H, oracle):
     off, tgt = G.rmat(13, seed=3)
-    assert np.diff(off).max() > 1024       # has hub segments at the default split
+    assert np.diff(off).max() > 1024       # has hub segments at this split
+    check_run(H, oracle, off, tgt, 6, frontier="auto", hub_min_deg=1024)
     check_run(H, oracle, off, tgt, 6, frontier="auto")
     check_run(H, oracle, off, tgt, 7, frontier="pull", hub_min_deg=64)
 
@@ -214,3 +215,15 @@ def test_async_gather_variant(H, oracle, log2m):
     for frontier in ("pull", "auto"):
         check_run(H, oracle, off, tgt, log2m, frontier=frontier, gather_variant=2,
                   small_max_deg=4, hub_min_deg=256)
+
+
+def test_autotune_picks_a_candidate_and_caches_it(H, oracle, tmp_path):
+    off, tgt = G.rmat(12, seed=13)
+    cache = tmp_path / "tune.txt"
+    best, ms = H.autotune(off, tgt, 6, SEED, cache_path=cache)
+    assert best["small_max_deg"] in (32, 128, 256, 1024, 4096)
+    assert best["hub_min_deg"] in (4096, 16384, 65536)
+    assert ms > 0 and cache.read_text().strip()
+    again, ms2 = H.autotune(off, tgt, 6, SEED, cache_path=cache)     # from the cache
+    assert again == best and ms2 == pytest.approx(ms)
+    check_run(H, oracle, off, tgt, 6, **best)
