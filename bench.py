@@ -357,6 +357,8 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
     ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--layout", default="byte", choices=["byte", "packed"],
+                    help="register layout: one byte each, or five bit-planes")
     ap.add_argument("--autotune", action="store_true",
                     help="pick degree split and gather variant with hanf_autotune first")
     ap.add_argument("--gather-ceiling", action="store_true",
@@ -398,6 +400,7 @@ def main():
     log2m, R = wl["log2m"], wl["runs"]
     m = 1 << log2m
     W = m * R
+    row_bytes = 5 * m // 8 if args.layout == "packed" else W   # bytes per stored counter row
     t_gen = time.perf_counter()
     off, tgt = make_graph(wl, args.seed + rank, device)
     torch.cuda.synchronize()
@@ -405,14 +408,15 @@ def main():
     n, arcs = off.numel() - 1, tgt.numel()
     stream = torch.cuda.current_stream(device)
 
-    tuned = {"gather_variant": args.gather_variant}
+    tuned = {"gather_variant": args.gather_variant, "layout": args.layout}
     tune_ms = None
     if args.autotune:
         from paper_1011_5599_gb300.hanf import autotune
         cache = os.path.join(ROOT, "paper_1011_5599_gb300", "_lib", "tune_cache.txt")
         t_tune = time.perf_counter()
         tuned, tune_ms = autotune(off, tgt, log2m, 0x5EED, cache_path=cache, device=device,
-                                  runs=R, frontier="auto")
+                                  runs=R, frontier="auto", layout=args.layout)
+        tuned["layout"] = args.layout
         print(json.dumps({"autotune": tuned, "best_ms": tune_ms,
                           "tuning_s": time.perf_counter() - t_tune}), file=sys.stderr)
     h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
@@ -438,7 +442,7 @@ def main():
             gathered += c["arcs_gathered"] * m * R
             union_ms += c["union_ms"]
             union_bytes += (4 * c["arcs_scanned"]
-                            + W * (c["arcs_gathered"] + c["own_reads"] + c["writes"]))
+                            + row_bytes * (c["arcs_gathered"] + c["own_reads"] + c["writes"]))
             launches += int(c["launches"])
             passes_list.append(int(c["passes"]))
             T_list.append(int(max(T)))
@@ -459,7 +463,7 @@ def main():
     if args.trace and args.driver == "host":
         h.run()
         for row in h.trace():
-            gbs = (4 * row["arcs_scanned"] + W * (row["arcs_gathered"] + row["own_reads"]
+            gbs = (4 * row["arcs_scanned"] + row_bytes * (row["arcs_gathered"] + row["own_reads"]
                                                   + row["writes"])) / (row["union_ms"] * 1e6)
             print(json.dumps({**row, "algorithmic_GBps": gbs}), file=sys.stderr)
     stat = {}
@@ -528,7 +532,7 @@ def main():
             "ms_per_step": 1e3 * elapsed_all / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": wl["text"], "n": n, "arcs": arcs, "m": m, "runs": R,
-                       "layout": "byte", "frontier": "auto", "driver": args.driver,
+                       "layout": args.layout, "frontier": "auto", "driver": args.driver,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (no flush)", "tuned": tuned,
                        "graph_gen_s": round(t_gen, 2)},

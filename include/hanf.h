@@ -84,6 +84,9 @@ typedef struct hanf_opts {
                               with 0 = the default, 1 = register batches,
                               2 = asynchronous copies into a shared-memory
                               ring (rows of at most 128 bytes)                */
+    int32_t layout;        /* 0 = one byte per register; 1 = five bit-planes of
+                              m bits (5m/8 bytes per counter; runs = 1 and
+                              m >= 32); results are identical               */
     const uint64_t *seeds; /* R explicit run seeds (host), or NULL             */
     void *stream;          /* cudaStream_t for every launch; NULL = default    */
 } hanf_opts;

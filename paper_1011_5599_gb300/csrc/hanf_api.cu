@@ -74,7 +74,7 @@ double hll_alpha(int m)
 
 struct Sizes {
     int64_t n, arcs;
-    int32_t log2m, m, R, W;
+    int32_t log2m, m, R, W, layout;
     int32_t d_small, d_hub, history;
     bool copy_graph, transpose, relabel;
     int64_t nwords, nred, ntiles, max_hub, max_seg, scan_elems;
@@ -109,10 +109,15 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     s->log2m = log2m;
     s->m = 1 << log2m;
     s->R = o.runs;
+    s->layout = o.layout;
+    if (o.layout < 0 || o.layout > 1) return fail(HANF_EINVAL, "layout=%d invalid", o.layout);
+    if (o.layout == 1 && (o.runs != 1 || log2m < 5))
+        return fail(HANF_EINVAL, "the bit-sliced layout needs runs = 1 and log2m >= 5");
     s->W = s->m * s->R;
-    if (s->W != 16 && s->W != 32 && s->W != 64 && s->W != 128 && s->W != 256 && s->W != 512 &&
+    if (o.layout == 0 && s->W != 16 && s->W != 32 && s->W != 64 && s->W != 128 && s->W != 256 && s->W != 512 &&
         s->W != 1024 && s->W != 2048)
         return fail(HANF_EINVAL, "runs * m = %d must be a power of two (runs 1, 2, 4 or 8)", s->W);
+    if (o.layout == 1) s->W = 5 * s->m / 8;
     s->d_small = o.small_max_deg ? o.small_max_deg : kDefaultSmall;
     s->d_hub = o.hub_min_deg ? o.hub_min_deg : kDefaultHub;
     if (s->d_hub < 2) return fail(HANF_EINVAL, "hub_min_deg=%d < 2", s->d_hub);
@@ -179,8 +184,10 @@ Layout make_layout(const Sizes &s)
         L.tgt2 = take(4 * std::max<int64_t>(s.arcs, 1));
         L.rcounts = take(8 * hanf::relabel_count_elems(s.n));
         L.roffs = take(8 * hanf::relabel_count_elems(s.n));
-        L.stage = take((size_t)std::min<int64_t>(s.n, kStageRows) * s.W);
     }
+    if (s.relabel || s.layout)
+        L.stage = take((size_t)std::min<int64_t>(std::max<int64_t>(s.n, 1), kStageRows) *
+                       std::max(s.W, s.m));
     L.total = at;
     return L;
 }
@@ -332,6 +339,7 @@ void hanf_default_opts(hanf_opts *o)
     o->dense_den = 0;
     o->relabel = 1;
     o->gather_variant = 0;
+    o->layout = 0;
     o->seeds = nullptr;
     o->stream = nullptr;
 }
@@ -391,6 +399,7 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.m = s.m;
     p.R = s.R;
     p.W = s.W;
+    p.layout = s.layout;
     p.nwords = s.nwords;
     p.nred = s.nred;
     p.frontier = o.frontier;
@@ -465,8 +474,8 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
         p.tgt = tgt2;
         p.orig_id = inv;
         c->perm = perm;
-        c->stage = ws + L.stage;
     }
+    if (s.relabel || s.layout) c->stage = ws + L.stage;
 
     // 2. degree classes -> [small | medium | hub] node lists
     int64_t tot[4] = {0, 0, 0, 0};
@@ -527,8 +536,9 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
         cudaMemcpyAsync(const_cast<double *>(p.lc), lc.data(), 8 * (s.m + 1),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
         return bail(fail(HANF_ECUDA, "constant upload failed"));
-    p.union_warps = hanf::union_occupancy_warps(s.W, c->nsm);
-    p.union_async_warps = hanf::union_async_warps(s.W, c->nsm);
+    p.union_warps = s.layout ? hanf::packed_occupancy_warps(s.m, c->nsm)
+                             : hanf::union_occupancy_warps(s.W, c->nsm);
+    p.union_async_warps = s.layout ? 0 : hanf::union_async_warps(s.W, c->nsm);
     p.warp_variant = (o.gather_variant == 2 && p.union_async_warps > 0) ? 2 : 1;
 
     rc = reset(c, s.history);
@@ -613,6 +623,17 @@ int hanf_registers(hanf_ctx *c, int32_t run, int64_t first, int64_t count, uint8
     if (rc) return rc;
     const uint8_t *regs = c->plan.regs[c->host_ctl.parity];
     const int W = c->plan.W, m = c->plan.m;
+    if (c->plan.layout) {
+        // bit-sliced storage: unpack one byte per register, chunk by chunk
+        for (int64_t i = 0; i < count; i += kStageRows) {
+            const int64_t k = std::min<int64_t>(kStageRows, count - i);
+            CU(hanf::launch_unpack_rows(regs, c->perm, first + i, k, m, c->stage, c->stream));
+            CU(cudaMemcpyAsync(out + i * m, c->stage, (size_t)k * m, cudaMemcpyDeviceToHost,
+                               c->stream));
+            CU(cudaStreamSynchronize(c->stream));
+        }
+        return HANF_OK;
+    }
     if (!c->perm) {
         const uint8_t *src = regs + first * W + (int64_t)run * m;
         CU(cudaMemcpy2DAsync(out, m, src, W, m, count, cudaMemcpyDeviceToHost, c->stream));

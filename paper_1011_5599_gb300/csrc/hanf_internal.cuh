@@ -41,7 +41,9 @@ struct DevCtl {
 // value, so a captured graph replays it unchanged.
 struct Plan {
     int64_t n, arcs;
-    int32_t b, m, R, W;               // W = R * m bytes per node row
+    int32_t b, m, R, W;               // W = bytes per stored node row: R * m (byte
+                                      // registers) or 5m/8 (bit-sliced, R = 1)
+    int32_t layout;                   // 0 byte registers, 1 five bit-planes
     int64_t nwords;                   // 64-node blocks = bitmap words
     int64_t nred;                     // first-level reduction CTAs per run
     const int64_t *off;
@@ -84,6 +86,7 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
                         cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch);
 int union_occupancy_warps(int W, int nsm);
+int packed_occupancy_warps(int m, int nsm);
 int union_async_warps(int W, int nsm);
 
 // Preprocessing (create time).
@@ -110,6 +113,8 @@ cudaError_t launch_relabel(const int64_t *off, const int32_t *tgt, int64_t n, in
 int64_t relabel_count_elems(int64_t n);
 cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
                                int64_t count, int W, uint8_t *out, cudaStream_t s);
+cudaError_t launch_unpack_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
+                               int64_t count, int m, uint8_t *out, cudaStream_t s);
 
 // Store the calling thread's message for hanf_last_error().
 void record_error(const char *msg);

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "hanf_internal.cuh"
 
@@ -1184,6 +1185,425 @@ int grid_for(int64_t work, int per_block, int64_t cap = 152 * 32)
     return (int)g;
 }
 
+// ---------------------------------------------------------------- 5-bit bit-sliced layout
+
+// A packed counter of m = 32P registers is five bit-planes of m bits (plane p
+// holds bit p of every register; register j is bit j%32 of word j/32):
+// 20P bytes instead of m.  The union compares two counters lexicographically
+// plane by plane from the top plane down, for 32 registers per word at once
+// (the parallel compare of Section 3.3 in bit-sliced form), and keeps the
+// larger register of every pair.
+template <int P>
+struct PRow {
+    uint32_t w[5][P];
+};
+
+template <int P>
+__device__ __forceinline__ void prow_zero(PRow<P> &r)
+{
+#pragma unroll
+    for (int p = 0; p < 5; ++p)
+#pragma unroll
+        for (int k = 0; k < P; ++k) r.w[p][k] = 0u;
+}
+
+template <int P>
+__device__ __forceinline__ void prow_load(PRow<P> &r, const uint8_t *base, int64_t row)
+{
+    const uint8_t *q = base + row * (20 * P);
+    if constexpr (P == 1) {
+        const uint32_t *s = reinterpret_cast<const uint32_t *>(q);
+#pragma unroll
+        for (int p = 0; p < 5; ++p) r.w[p][0] = __ldg(s + p);
+    } else if constexpr (P == 2) {
+        const uint2 *s = reinterpret_cast<const uint2 *>(q);
+#pragma unroll
+        for (int p = 0; p < 5; ++p) {
+            const uint2 x = __ldg(s + p);
+            r.w[p][0] = x.x;
+            r.w[p][1] = x.y;
+        }
+    } else {
+        const uint4 *s = reinterpret_cast<const uint4 *>(q);
+#pragma unroll
+        for (int p = 0; p < 5; ++p)
+#pragma unroll
+            for (int k = 0; k < P / 4; ++k) {
+                const uint4 x = __ldg(s + p * (P / 4) + k);
+                r.w[p][4 * k] = x.x;
+                r.w[p][4 * k + 1] = x.y;
+                r.w[p][4 * k + 2] = x.z;
+                r.w[p][4 * k + 3] = x.w;
+            }
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void prow_store(uint8_t *base, int64_t row, const PRow<P> &r)
+{
+    uint8_t *q = base + row * (20 * P);
+    if constexpr (P == 1) {
+        uint32_t *s = reinterpret_cast<uint32_t *>(q);
+#pragma unroll
+        for (int p = 0; p < 5; ++p) s[p] = r.w[p][0];
+    } else if constexpr (P == 2) {
+        uint2 *s = reinterpret_cast<uint2 *>(q);
+#pragma unroll
+        for (int p = 0; p < 5; ++p) s[p] = make_uint2(r.w[p][0], r.w[p][1]);
+    } else {
+        uint4 *s = reinterpret_cast<uint4 *>(q);
+#pragma unroll
+        for (int p = 0; p < 5; ++p)
+#pragma unroll
+            for (int k = 0; k < P / 4; ++k)
+                s[p * (P / 4) + k] = make_uint4(r.w[p][4 * k], r.w[p][4 * k + 1], r.w[p][4 * k + 2],
+                                                r.w[p][4 * k + 3]);
+    }
+}
+
+// a <- register-wise max(a, b): lt marks registers where a < b, found at the
+// highest plane where they differ; there b's bits are taken.
+template <int P>
+__device__ __forceinline__ void prow_max(PRow<P> &a, const PRow<P> &b)
+{
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        uint32_t lt = 0u, eq = 0xffffffffu;
+#pragma unroll
+        for (int p = 4; p >= 0; --p) {
+            const uint32_t x = a.w[p][k], y = b.w[p][k];
+            lt |= eq & ~x & y;
+            eq &= ~(x ^ y);
+        }
+#pragma unroll
+        for (int p = 0; p < 5; ++p) a.w[p][k] = (a.w[p][k] & ~lt) | (b.w[p][k] & lt);
+    }
+}
+
+template <int P>
+__device__ __forceinline__ bool prow_eq(const PRow<P> &a, const PRow<P> &b)
+{
+    uint32_t d = 0u;
+#pragma unroll
+    for (int p = 0; p < 5; ++p)
+#pragma unroll
+        for (int k = 0; k < P; ++k) d |= a.w[p][k] ^ b.w[p][k];
+    return d == 0u;
+}
+
+template <int P>
+__device__ __forceinline__ void prow_warp_max(PRow<P> &r)
+{
+#pragma unroll
+    for (int s = 16; s; s >>= 1) {
+        PRow<P> o;
+#pragma unroll
+        for (int p = 0; p < 5; ++p)
+#pragma unroll
+            for (int k = 0; k < P; ++k) o.w[p][k] = __shfl_xor_sync(kFull, r.w[p][k], s);
+        prow_max(r, o);
+    }
+}
+
+// New packed counter of v; the single-run analogue of node_finish (lane-level).
+template <int P>
+__device__ __forceinline__ uint32_t pnode_finish(const Plan &p, int cur, const PRow<P> &acc,
+                                                 bool need, bool inR, int32_t v, uint32_t &c_own,
+                                                 uint32_t &c_write, const PRow<P> *pre = nullptr)
+{
+    if (!need) return 0u;
+    PRow<P> own;
+    if (pre) own = *pre;
+    else prow_load(own, p.regs[cur], v);
+    PRow<P> nw = own;
+    prow_max(nw, acc);
+    const bool changed = !prow_eq(nw, own);
+    if (changed || inR) {
+        prow_store(p.regs[cur ^ 1], v, nw);
+        ++c_write;
+    }
+    ++c_own;
+    return changed ? 1u : 0u;
+}
+
+// Small nodes: a lane per node, U arcs in flight per lane.
+template <int P>
+__global__ void __launch_bounds__(kBlock, 3) k_punion_small(Plan p)
+{
+    constexpr int U = P <= 2 ? 4 : (P == 4 ? 2 : 1);
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const bool test = ctl->mode != kModeDense;
+    const bool push = ctl->mode == kModePush;
+    const bool own_early = !test || push;
+    const uint8_t *rc = p.regs[cur];
+    const unsigned long long *Fc = p.F[cur];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int32_t *list = push ? p.cand_list[0] : p.nodes;
+    const int64_t count = push ? (int64_t)ctl->cand_count[0] : p.n_small;
+    uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    for (int64_t base = warp * 32; base < count; base += nwarps * 32) {
+        const int64_t idx = base + lane;
+        const bool valid = idx < count;
+        const int32_t v = valid ? __ldg(list + idx) : 0;
+        PRow<P> own, acc;
+        if (valid && own_early) prow_load(own, rc, v);
+        prow_zero(acc);
+        bool any = false;
+        if (valid) {
+            const int64_t beg = __ldg(p.off + v), end = __ldg(p.off + v + 1);
+            c_scan += (uint32_t)(end - beg);
+            for (int64_t e = beg; e < end; e += U) {
+                int32_t w[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    w[u] = e + u < end ? __ldg(p.tgt + e + u) : -1;
+                    if (w[u] >= 0 && test && !test_bit(Fc, w[u])) w[u] = -1;
+                }
+                PRow<P> x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (w[u] >= 0) prow_load(x[u], rc, w[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (w[u] >= 0) {
+                        prow_max(acc, x[u]);
+                        any = true;
+                        ++c_gather;
+                    }
+            }
+        }
+        const bool inR = valid && !first && test_bit(Fc, v);
+        const uint32_t mask = pnode_finish(p, cur, acc, valid && (any || inR), inR, v, c_own,
+                                           c_write, own_early ? &own : nullptr);
+        warp_mark(p, cur, valid, v, mask);
+    }
+    flush_counters(p, c_scan, c_gather, c_own, c_write);
+}
+
+// Medium nodes and hub segments: a warp per item, lane i merges arcs
+// e+i, e+i+32, ... (U per lane in flight), then a warp-wide max.
+template <int P>
+__global__ void __launch_bounds__(kBlock, 3) k_punion_warp(Plan p)
+{
+    constexpr int U = P <= 2 ? 4 : (P == 4 ? 2 : 1);
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const bool test = ctl->mode != kModeDense;
+    const bool push = ctl->mode == kModePush;
+    const uint8_t *rc = p.regs[cur];
+    const unsigned long long *Fc = p.F[cur];
+    const int32_t *med = push ? p.cand_list[1] : p.nodes + p.n_small;
+    const int64_t total = p.n_seg + (push ? (int64_t)ctl->cand_count[1] : p.n_med);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    for (int64_t it = warp; it < total; it += nwarps) {
+        const bool seg = it < p.n_seg;
+        const int32_t v = seg ? __ldg(p.seg_node + it) : __ldg(med + (it - p.n_seg));
+        const bool take = !seg || !push || test_bit(p.cand, v);
+        PRow<P> acc;
+        prow_zero(acc);
+        bool any = false;
+        if (take) {
+            const int64_t beg = seg ? __ldg(p.seg_beg + it) : __ldg(p.off + v);
+            const int64_t end = seg ? __ldg(p.seg_end + it) : __ldg(p.off + v + 1);
+            if (lane == 0) c_scan += (uint32_t)(end - beg);
+            for (int64_t e = beg + lane; e < end; e += 32 * U) {
+                int32_t w[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    w[u] = e + 32 * u < end ? __ldg(p.tgt + e + 32 * u) : -1;
+                    if (w[u] >= 0 && test && !test_bit(Fc, w[u])) w[u] = -1;
+                }
+                PRow<P> x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (w[u] >= 0) prow_load(x[u], rc, w[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (w[u] >= 0) {
+                        prow_max(acc, x[u]);
+                        any = true;
+                        ++c_gather;
+                    }
+            }
+        }
+        prow_warp_max(acc);
+        any = __any_sync(kFull, any);
+        if (seg) {
+            if (lane == 0) {
+                prow_store(p.hub_part, it, acc);
+                p.hub_any[it] = any ? 1 : 0;
+            }
+        } else {
+            const bool inR = take && !first && test_bit(Fc, v);
+            const bool need = take && (any || inR) && lane == 0;
+            const uint32_t mask = pnode_finish(p, cur, acc, need, inR, v, c_own, c_write);
+            warp_mark(p, cur, lane == 0, v, mask);
+        }
+    }
+    flush_counters(p, c_scan, c_gather, c_own, c_write);
+}
+
+// Hub nodes: combine the segment partials, a lane per hub.
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_phub_finish(Plan p)
+{
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done || p.n_hub == 0) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const bool push = ctl->mode == kModePush;
+    const unsigned long long *Fc = p.F[cur];
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    uint32_t c_own = 0, c_write = 0;
+    for (int64_t base = tid - (threadIdx.x & 31); base < p.n_hub; base += nthreads) {
+        const int64_t h = base + (threadIdx.x & 31);
+        const bool valid = h < p.n_hub;
+        const int32_t v = valid ? p.nodes[p.n_small + p.n_med + h] : 0;
+        const bool take = valid && (!push || test_bit(p.cand, v));
+        PRow<P> acc;
+        prow_zero(acc);
+        bool any = false;
+        if (take) {
+            for (int32_t s = p.hub_seg_first[h]; s < p.hub_seg_first[h + 1]; ++s) {
+                if (p.hub_any[s]) {
+                    PRow<P> x;
+                    prow_load(x, p.hub_part, s);
+                    prow_max(acc, x);
+                    any = true;
+                }
+            }
+        }
+        const bool inR = take && !first && test_bit(Fc, v);
+        const uint32_t mask = pnode_finish(p, cur, acc, take && (any || inR), inR, v, c_own, c_write);
+        warp_mark(p, cur, valid, v, mask);
+    }
+    flush_counters(p, 0u, 0u, c_own, c_write);
+}
+
+// size() of a packed counter: V = empty registers; sum_j 2^(31-M[j]) taken
+// value by value from the planes.
+template <int P>
+__device__ __forceinline__ double pnode_size(const Plan &p, const uint8_t *rc, int64_t v)
+{
+    PRow<P> r;
+    prow_load(r, rc, v);
+    unsigned long long S = 0;
+    int V = 0;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        V += __popc(~(r.w[0][k] | r.w[1][k] | r.w[2][k] | r.w[3][k] | r.w[4][k]));
+        for (int M = 0; M < 32; ++M) {
+            uint32_t sel = 0xffffffffu;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) sel &= ((M >> b) & 1) ? r.w[b][k] : ~r.w[b][k];
+            S += (unsigned long long)__popc(sel) << (31 - M);
+        }
+    }
+    const double sum = (double)S * 0x1p-31;
+    const double Z = 1.0 / sum;
+    double E = p.amm * Z;
+    if (E <= 2.5 * (double)p.m && V > 0) E = p.lc[V];
+    return E;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
+{
+    DevCtl *c = p.ctl;
+    if (c->done) return;
+    const bool all = c->t == 0;
+    const uint8_t *rc = p.regs[c->parity];
+    const unsigned long long *Fc = p.F[c->parity];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t blk = warp; blk < p.nwords; blk += nwarps) {
+        if (!all && Fc[blk] == 0ull) continue;
+        const int64_t v0 = blk * 64 + lane, v1 = v0 + 32;
+        if (!all && p.in_off) {
+            const unsigned long long word = Fc[blk];
+            unsigned long long d = 0;
+            if ((word >> lane) & 1ull) d += (unsigned long long)(p.in_off[v0 + 1] - p.in_off[v0]);
+            if ((word >> (lane + 32)) & 1ull) d += (unsigned long long)(p.in_off[v1 + 1] - p.in_off[v1]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+            if (lane == 0 && d) atomicAdd(&p.ctl->changed_in_arcs, d);
+        }
+        double s = (v0 < p.n ? pnode_size<P>(p, rc, v0) : 0.0) +
+                   (v1 < p.n ? pnode_size<P>(p, rc, v1) : 0.0);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane == 0) p.blk_part[blk] = s;
+    }
+}
+
+// Algorithm 2's initialisation in the packed layout: node v adds itself.
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_pinit(Plan p)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t item = p.orig_id ? (uint64_t)__ldg(p.orig_id + v) : (uint64_t)v;
+        const uint64_t h = splitmix64(item ^ p.seeds[0]);
+        const int idx = (int)(h >> (64 - p.b));
+        const uint64_t rest = h << p.b;
+        int rho = rest ? __clzll((long long)rest) + 1 : 64 - p.b + 1;
+        rho = rho > 31 ? 31 : rho;
+        PRow<P> r;
+        prow_zero(r);
+#pragma unroll
+        for (int b = 0; b < 5; ++b)
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+                if (k == (idx >> 5) && ((rho >> b) & 1)) r.w[b][k] = 1u << (idx & 31);
+        prow_store(p.regs[0], v, r);
+        prow_store(p.regs[1], v, r);
+    }
+}
+
+// Registers of stored rows perm[first..first+count) (or first.. without a
+// permutation) unpacked to one byte each.
+template <int P>
+__global__ void k_punpack(const uint8_t *regs, const int32_t *perm, int64_t first, int64_t count,
+                          uint8_t *out)
+{
+    constexpr int m = 32 * P;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count * m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t node = i / m;
+        const int j = (int)(i - node * m);
+        const int64_t row = perm ? perm[first + node] : first + node;
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(regs + row * (20 * P));
+        uint32_t val = 0;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) val |= ((q[b * P + (j >> 5)] >> (j & 31)) & 1u) << b;
+        out[i] = (uint8_t)val;
+    }
+}
+
+template <typename F>
+cudaError_t with_planes(int m, F &&f)
+{
+    switch (m) {
+    case 32: return f(std::integral_constant<int, 1>());
+    case 64: return f(std::integral_constant<int, 2>());
+    case 128: return f(std::integral_constant<int, 4>());
+    case 256: return f(std::integral_constant<int, 8>());
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // ---------------------------------------------------------------- dispatch on row width
 
 template <int LANES, int VPL>
@@ -1277,6 +1697,20 @@ int union_async_warps(int W, int nsm)
     return nb * nsm * (kBlock / 32);
 }
 
+int packed_occupancy_warps(int m, int nsm)
+{
+    int nb = 0;
+    with_planes(m, [&](auto P) {
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_punion_small<decltype(P)::value>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_punion_warp<decltype(P)::value>, kBlock, 0);
+        nb = a < b ? a : b;
+        return cudaSuccess;
+    });
+    if (nb < 1) nb = 1;
+    return nb * nsm * (kBlock / 32);
+}
+
 int union_occupancy_warps(int W, int nsm)
 {
     int nb = 0;
@@ -1296,13 +1730,27 @@ cudaError_t launch_validate(const Plan &p, cudaStream_t s)
 
 cudaError_t launch_init(const Plan &p, cudaStream_t s)
 {
+    if (p.layout) {
+        return with_planes(p.m, [&](auto P) {
+            k_pinit<decltype(P)::value><<<grid_for(p.n, kBlock, 152 * 64), kBlock, 0, s>>>(p);
+            return cudaGetLastError();
+        });
+    }
     k_init<<<grid_for(p.n * (p.W >> 4), kBlock, 152 * 64), kBlock, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
 {
-    k_est_blocks<<<grid_for(p.nwords * p.R, kBlock / 32, 152 * 64), kBlock, 0, s>>>(p);
+    if (p.layout) {
+        cudaError_t err = with_planes(p.m, [&](auto P) {
+            k_pest_blocks<decltype(P)::value><<<grid_for(p.nwords, kBlock / 32, 152 * 64), kBlock, 0, s>>>(p);
+            return cudaGetLastError();
+        });
+        if (err != cudaSuccess) return err;
+    } else {
+        k_est_blocks<<<grid_for(p.nwords * p.R, kBlock / 32, 152 * 64), kBlock, 0, s>>>(p);
+    }
     k_est_reduce1<<<dim3((unsigned)p.nred, (unsigned)p.R), kBlock, 0, s>>>(p);
     k_est_reduce2<<<p.R, kBlock, 0, s>>>(p);
     if (nlaunch) *nlaunch += 3;
@@ -1316,12 +1764,27 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     k_clear<<<grid_for(p.nwords, kBlock, 152 * 16), kBlock, 0, s>>>(p);
     if (p.in_off) k_mark<<<grid_for(p.nwords, kBlock / 32, 152 * 8), kBlock, 0, s>>>(p);
     if (ev0) cudaEventRecord(ev0, s);
-    cudaError_t err = with_width(p.W, [&](auto k) { return decltype(k)::launch(p, s); });
-    if (err != cudaSuccess) return err;
-    if (p.n_hub) {
-        err = with_width(p.W, [&](auto k) { return decltype(k)::launch_hub(p, s); });
-        if (err != cudaSuccess) return err;
+    cudaError_t err;
+    if (p.layout) {
+        err = with_planes(p.m, [&](auto P) {
+            constexpr int PP = decltype(P)::value;
+            constexpr int WPB = kBlock / 32;
+            const int64_t persistent = (p.union_warps * 32 + kBlock - 1) / kBlock;
+            const int64_t wi = p.n_seg + p.n_med, si = (p.n_small + 31) / 32;
+            const int blocks = (int)std::max<int64_t>(1, std::min(persistent, (wi + WPB - 1) / WPB));
+            const int sblocks = (int)std::max<int64_t>(1, std::min(persistent, (si + WPB - 1) / WPB));
+            k_punion_warp<PP><<<blocks, kBlock, 0, s>>>(p);
+            k_punion_small<PP><<<sblocks, kBlock, 0, s>>>(p);
+            if (p.n_hub)
+                k_phub_finish<PP><<<grid_for(p.n_hub, kBlock, 152 * 16), kBlock, 0, s>>>(p);
+            return cudaGetLastError();
+        });
+    } else {
+        err = with_width(p.W, [&](auto k) { return decltype(k)::launch(p, s); });
+        if (err == cudaSuccess && p.n_hub)
+            err = with_width(p.W, [&](auto k) { return decltype(k)::launch_hub(p, s); });
     }
+    if (err != cudaSuccess) return err;
     if (ev1) cudaEventRecord(ev1, s);
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
     if (nlaunch)
@@ -1441,6 +1904,17 @@ cudaError_t launch_relabel(const int64_t *off, const int32_t *tgt, int64_t n, in
 }
 
 int64_t relabel_count_elems(int64_t n) { return kHotClasses * classify_blocks(n) + 1; }
+
+cudaError_t launch_unpack_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
+                               int64_t count, int m, uint8_t *out, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    return with_planes(m, [&](auto P) {
+        k_punpack<decltype(P)::value><<<grid_for(count * m, kBlock, 152 * 32), kBlock, 0, s>>>(
+            regs, perm, first, count, out);
+        return cudaGetLastError();
+    });
+}
 
 cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
                                int64_t count, int W, uint8_t *out, cudaStream_t s)

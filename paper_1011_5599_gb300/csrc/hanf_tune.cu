@@ -41,8 +41,8 @@ std::string shape_key(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o
     const int ln = n > 0 ? (int)std::lround(std::log2((double)n)) : 0;
     const int la = arcs > 0 ? (int)std::lround(std::log2((double)arcs)) : 0;
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|W%d|n2^%d|a2^%d|f%d|r%d", gpu.c_str(), W, ln, la, o.frontier,
-             o.relabel);
+    snprintf(buf, sizeof buf, "%s|W%d|L%d|n2^%d|a2^%d|f%d|r%d", gpu.c_str(), W, o.layout, ln, la,
+             o.frontier, o.relabel);
     return buf;
 }
 
@@ -105,7 +105,7 @@ extern "C" int hanf_autotune(int64_t n, int64_t arcs, const int64_t *offsets,
     for (int32_t vsm : smalls)
         for (int32_t vh : hubs)
             for (int32_t gv : variants) {
-                if (gv == 2 && (1 << log2m) * o.runs > 128) continue;   // rows too wide
+                if (gv == 2 && ((1 << log2m) * o.runs > 128 || o.layout)) continue;   // not applicable
                 hanf_opts c = o;
                 c.small_max_deg = vsm;
                 c.hub_min_deg = vh;

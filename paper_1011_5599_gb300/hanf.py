@@ -54,7 +54,7 @@ class Opts(ctypes.Structure):
                 ("hub_min_deg", ctypes.c_int32), ("history_cap", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("dense_den", ctypes.c_int32), ("relabel", ctypes.c_int32),
-                ("gather_variant", ctypes.c_int32),
+                ("gather_variant", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("seeds", ctypes.POINTER(ctypes.c_uint64)), ("stream", ctypes.c_void_p)]
 
 
@@ -139,7 +139,7 @@ def default_opts() -> Opts:
 
 def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=0,
               history_cap=0, use_graph=False, profile=False, seeds=None, stream=None,
-              dense_den=0, relabel=True, gather_variant=0):
+              dense_den=0, relabel=True, gather_variant=0, layout=0):
     o = default_opts()
     o.runs = runs
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
@@ -152,6 +152,7 @@ def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=
     o.dense_den = dense_den
     o.relabel = int(bool(relabel))
     o.gather_variant = gather_variant
+    o.layout = {"byte": 0, "packed": 1}.get(layout, layout) if isinstance(layout, str) else layout
     keep = None
     if seeds is not None:
         keep = (ctypes.c_uint64 * len(seeds))(*[int(s) & (2**64 - 1) for s in seeds])
@@ -201,7 +202,8 @@ class HyperANF:
                  frontier="auto", push_den: int = 4, small_max_deg: int = 0,
                  hub_min_deg: int = 0, history_cap: int = 0, use_graph: bool = False,
                  profile: bool = False, seeds=None, device=None, stream=None,
-                 dense_den: int = 0, relabel: bool = True, gather_variant: int = 0):
+                 dense_den: int = 0, relabel: bool = True, gather_variant: int = 0,
+                 layout=0):
         import torch
 
         self.device = torch.device(device if device is not None else "cuda")
@@ -229,7 +231,7 @@ class HyperANF:
         self._opts, self._seed_keep = make_opts(runs, frontier, push_den, small_max_deg,
                                                 hub_min_deg, history_cap, use_graph, profile,
                                                 seeds, self.stream.cuda_stream, dense_den,
-                                                relabel, gather_variant)
+                                                relabel, gather_variant, layout)
         size = workspace_size(n, arcs, log2m, self._opts, not on_dev)
         self.workspace_bytes = size
         with torch.cuda.device(self.device):

@@ -227,3 +227,43 @@ def test_autotune_picks_a_candidate_and_caches_it(H, oracle, tmp_path):
     again, ms2 = H.autotune(off, tgt, 6, SEED, cache_path=cache)     # from the cache
     assert again == best and ms2 == pytest.approx(ms)
     check_run(H, oracle, off, tgt, 6, **best)
+
+
+@pytest.mark.parametrize("log2m", [5, 6, 7, 8])
+@pytest.mark.parametrize("frontier", ["off", "pull", "auto"])
+def test_bit_sliced_layout(H, oracle, log2m, frontier):
+    """Five bit-planes per counter give the same registers, T and N(t)."""
+    off, tgt = G.rmat(12, seed=14)
+    check_run(H, oracle, off, tgt, log2m, frontier=frontier, layout="packed")
+
+
+def test_bit_sliced_layout_degree_paths(H, oracle):
+    off, tgt = G.web(1 << 12, seed=15)
+    for small, hub in [(1, 2), (2, 8), (4096, 1 << 20)]:
+        check_run(H, oracle, off, tgt, 6, layout="packed", small_max_deg=small, hub_min_deg=hub)
+    check_run(H, oracle, off, tgt, 6, layout="packed", relabel=False, use_graph=True)
+    check_run(H, oracle, *G.clique_path(35, 3), 8, layout="packed")
+    check_run(H, oracle, *G.empty(70), 6, layout="packed")
+
+
+def test_bit_sliced_every_pass(H, oracle):
+    off, tgt = G.er(3000, 12000, seed=16)
+    c = oracle.init(off.size - 1, 6, oracle.run_seed(SEED, 0))
+    with H.HyperANF(off, tgt, 6, SEED, layout="packed") as h:
+        while True:
+            assert np.array_equal(h.registers(0), c)
+            np.testing.assert_allclose(h.estimate()[0], oracle.sum_sizes(c), rtol=RTOL)
+            ch = h.iterate()
+            c, ch_o = oracle.union_pass(off, tgt, c)
+            assert ch == ch_o
+            if ch == 0:
+                break
+
+
+def test_bit_sliced_layout_rejects_unsupported(H):
+    off, tgt = G.er(100, 300, seed=1)
+    for kw in [dict(layout="packed", runs=2), dict(layout="packed", log2m=4)]:
+        log2m = kw.pop("log2m", 6)
+        with pytest.raises(H.HanfError) as e:
+            H.HyperANF(off, tgt, log2m, **kw)
+        assert e.value.code == H.HANF_EINVAL
