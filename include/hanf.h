@@ -258,6 +258,36 @@ HANF_API int hanf_server_stats(hanf_server *s, double *out, int32_t nout);
  * free the server.  No other call on the server may be in progress. */
 HANF_API void hanf_server_destroy(hanf_server *s);
 
+/* Checkpoint and resume (Algorithm 2 keeps its state in the counters and the
+ * update file; this is the GPU analogue): the state after any pass -- both
+ * counter buffers, the changed-node bitmaps, the N(t) history, the
+ * estimator's block partials and the control block -- is copied to a host
+ * buffer of hanf_checkpoint_size() bytes, and can be loaded into a context
+ * created on the same graph with the same log2m, runs, seeds, layout and
+ * relabelling (checked: HANF_EINVAL otherwise).  hanf_continue then runs
+ * passes from the current state, like hanf_run without re-initialising; a
+ * resumed run gives bit-identical counters, T and N(t).  All synchronise. */
+HANF_API int hanf_checkpoint_size(hanf_ctx *ctx, size_t *bytes_out);
+HANF_API int hanf_checkpoint_save(hanf_ctx *ctx, void *buf, size_t bytes);
+HANF_API int hanf_checkpoint_load(hanf_ctx *ctx, const void *buf, size_t bytes);
+HANF_API int hanf_continue(hanf_ctx *ctx, int32_t max_iter, double *N_out, int32_t cap,
+                           int32_t *T_out);
+
+/* Algorithm 3 (Section 4, Corollary 2): with each N(t) known to relative
+ * error eps, M = max_t N(t), *lo = the largest D- with N(D-)/M <= alpha(1-2eps)
+ * and *hi = the smallest D+ with N(D+)/M >= alpha(1+2eps); the effective
+ * diameter at alpha lies in [D-..D+] with confidence 1-3 delta.  -1 where no
+ * such t exists (no lower end; no upper end within 0..T).  No GPU. */
+HANF_API int hanf_ed_interval(const double *N, int32_t T, double alpha, double eps, int32_t *lo,
+                              int32_t *hi);
+
+/* Statistics over R runs (Section 4's advice to average many runs; Table 2
+ * reports means and standard deviations): N is R x cap row-major with run r's
+ * N_r(0..T_r) in row r.  out10 = {mean of ed, ied, mean distance, variance,
+ * spid, then their sample standard deviations (0 if R = 1)}.  No GPU. */
+HANF_API int hanf_stats_runs(const double *N, int32_t R, int32_t cap, const int32_t *T,
+                             double alpha, int32_t exclude_zero, double *out10);
+
 /* Release the context (not the workspace, which belongs to the caller). */
 HANF_API void hanf_destroy(hanf_ctx *ctx);
 

@@ -360,3 +360,21 @@ ORA_API void ora_stats(const double *N, int32_t T, double alpha, int32_t exclude
     out[3] = sq - mean * mean;
     out[4] = out[3] / mean;
 }
+
+/* Algorithm 3 (Section 4): M = max_t N(t); D- is the largest t with
+ * N(t)/M <= alpha(1-2 eps), D+ the smallest t with N(t)/M >= alpha(1+2 eps);
+ * -1 when there is none. */
+ORA_API void ora_ed_interval(const double *N, int32_t T, double alpha, double eps, int32_t *lo,
+                             int32_t *hi)
+{
+    double M = -INFINITY;
+    int32_t t;
+    *lo = -1;
+    *hi = -1;
+    for (t = 0; t <= T; ++t)
+        if (N[t] > M) M = N[t];
+    for (t = T; t >= 0; --t)
+        if (N[t] / M <= alpha * (1.0 - 2.0 * eps)) { *lo = t; break; }
+    for (t = 0; t <= T; ++t)
+        if (N[t] / M >= alpha * (1.0 + 2.0 * eps)) { *hi = t; break; }
+}

@@ -85,6 +85,9 @@ def _load():
         lib.ora_symmetric_final_sum.restype = ctypes.c_double
         lib.ora_symmetric_final_sum.argtypes = [_i64p, _i32p, ctypes.c_int64, ctypes.c_int32,
                                                 ctypes.c_uint64]
+        lib.ora_ed_interval.restype = None
+        lib.ora_ed_interval.argtypes = [_f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                        _i32p, _i32p]
         lib.ora_stats.restype = None
         lib.ora_stats.argtypes = [_f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                   _f64p]
@@ -229,3 +232,21 @@ def hyperanf_runs(offsets, targets, b: int, seed: int, R: int, cap: int = 4096,
     """R independent runs with seed_r = splitmix64(seed + r)."""
     return [hyperanf(offsets, targets, b, run_seed(seed, r), cap=cap, threads=threads)[:2]
             for r in range(R)]
+
+
+def ed_interval(N, alpha_: float = 0.9, eps: float = 0.0):
+    """Algorithm 3's bracket [D-, D+] of the effective diameter."""
+    N = np.ascontiguousarray(N, dtype=np.float64)
+    lo, hi = ctypes.c_int32(), ctypes.c_int32()
+    _load().ora_ed_interval(_p(N, _f64p), N.size - 1, alpha_, eps, ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def stats_runs(N_runs, alpha_: float = 0.9, exclude_zero: bool = False) -> dict:
+    """Mean and sample standard deviation over runs of each statistic."""
+    per = [stats(N, alpha_, exclude_zero) for N in N_runs]
+    out = {}
+    for k in ("ed", "ied", "mean", "var", "spid"):
+        x = np.array([p[k] for p in per])
+        out[k] = (float(x.mean()), float(x.std(ddof=1)) if len(x) > 1 else 0.0)
+    return out

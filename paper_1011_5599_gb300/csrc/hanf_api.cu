@@ -574,6 +574,14 @@ int hanf_iterate(hanf_ctx *c, int64_t *changed_out)
     return HANF_OK;
 }
 
+namespace {
+
+// Run passes from the current state until stabilisation (or ctl.max_t), then
+// copy N(0..T) and the T_r out.
+int drive(hanf_ctx *c, double *N_out, int32_t cap, int32_t *T_out, int32_t max_iter);
+
+}  // namespace
+
 int hanf_run(hanf_ctx *c, int32_t max_iter, double *N_out, int32_t cap, int32_t *T_out)
 {
     if (!c || !N_out || !T_out) return fail(HANF_EINVAL, "NULL argument");
@@ -581,7 +589,44 @@ int hanf_run(hanf_ctx *c, int32_t max_iter, double *N_out, int32_t cap, int32_t 
     const int32_t max_t = std::min<int32_t>(std::min(max_iter, cap), c->sz.history);
     int rc = reset(c, max_t);
     if (rc) return rc;
-    if (c->opts.use_graph) {
+    return drive(c, N_out, cap, T_out, max_iter);
+}
+
+int hanf_continue(hanf_ctx *c, int32_t max_iter, double *N_out, int32_t cap, int32_t *T_out)
+{
+    if (!c || !N_out || !T_out) return fail(HANF_EINVAL, "NULL argument");
+    if (cap < 1 || max_iter < 1) return fail(HANF_EINVAL, "cap and max_iter must be >= 1");
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    DevCtl h = c->host_ctl;
+    h.max_t = std::min<int32_t>(std::min<int64_t>((int64_t)h.t + max_iter, cap), c->sz.history);
+    const bool limited = h.err == HANF_ERANGE && h.t < h.max_t;
+    if (limited) {   // resume after a run that hit its pass limit
+        h.err = HANF_OK;
+        h.done = 0;
+    }
+    CU(cudaMemcpyAsync(c->plan.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    if (limited) {
+        // that run stopped before estimating N(t) at its last t
+        int nl = 0;
+        CU(hanf::launch_estimate(c->plan, c->stream, &nl));
+        c->launches += nl;
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    c->host_ctl = h;
+    return drive(c, N_out, cap, T_out, max_iter);
+}
+
+}  // extern "C"
+
+namespace {
+
+int drive(hanf_ctx *c, double *N_out, int32_t cap, int32_t *T_out, int32_t max_iter)
+{
+    int rc = HANF_OK;
+    if (c->host_ctl.done) {
+        // already stable (or stopped): nothing to run
+    } else if (c->opts.use_graph) {
         rc = build_graph(c);
         if (rc) return rc;
         CU(cudaGraphLaunch(c->gexec, c->stream));
@@ -611,6 +656,10 @@ int hanf_run(hanf_ctx *c, int32_t max_iter, double *N_out, int32_t cap, int32_t 
     if (h.err) return fail(HANF_ERANGE, "no stabilisation within %d passes / %d values", max_iter, cap);
     return HANF_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int hanf_registers(hanf_ctx *c, int32_t run, int64_t first, int64_t count, uint8_t *out)
 {
@@ -708,6 +757,157 @@ int hanf_stats(const double *N, int32_t T, double alpha, int32_t exclude_zero, d
     out5[2] = mean;
     out5[3] = second - mean * mean;
     out5[4] = out5[3] / mean;
+    return HANF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct CkpHeader {
+    char magic[8];
+    int64_t n, arcs, nwords;
+    int32_t log2m, R, layout, relabel, W, history;
+    uint64_t seeds[hanf::kMaxRuns];
+};
+
+struct CkpParts {
+    size_t header, ctl, regs, bits, hist, blk, total;
+};
+
+CkpParts ckp_parts(const hanf_ctx *c)
+{
+    const Plan &p = c->plan;
+    CkpParts q;
+    q.header = sizeof(CkpHeader);
+    q.ctl = sizeof(DevCtl);
+    q.regs = (size_t)std::max<int64_t>(p.n, 1) * p.W;
+    q.bits = (size_t)p.nwords * 8;
+    q.hist = (size_t)p.history_cap * p.R * 8;
+    q.blk = (size_t)p.nwords * p.R * 8;
+    q.total = q.header + q.ctl + 2 * q.regs + 2 * q.bits + q.hist + q.blk;
+    return q;
+}
+
+CkpHeader ckp_header(const hanf_ctx *c)
+{
+    CkpHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "HANFCKP1", 8);
+    h.n = c->plan.n;
+    h.arcs = c->plan.arcs;
+    h.nwords = c->plan.nwords;
+    h.log2m = c->plan.b;
+    h.R = c->plan.R;
+    h.layout = c->plan.layout;
+    h.relabel = c->perm != nullptr;
+    h.W = c->plan.W;
+    h.history = c->plan.history_cap;
+    for (int r = 0; r < c->plan.R; ++r) h.seeds[r] = c->seeds[r];
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hanf_checkpoint_size(hanf_ctx *c, size_t *bytes_out)
+{
+    if (!c || !bytes_out) return fail(HANF_EINVAL, "NULL argument");
+    *bytes_out = ckp_parts(c).total;
+    return HANF_OK;
+}
+
+int hanf_checkpoint_save(hanf_ctx *c, void *buf, size_t bytes)
+{
+    if (!c || !buf) return fail(HANF_EINVAL, "NULL argument");
+    const CkpParts q = ckp_parts(c);
+    if (bytes < q.total) return fail(HANF_ENOMEM, "checkpoint needs %zu bytes", q.total);
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    uint8_t *o = static_cast<uint8_t *>(buf);
+    const CkpHeader h = ckp_header(c);
+    std::memcpy(o, &h, sizeof h);
+    std::memcpy(o + q.header, &c->host_ctl, sizeof(DevCtl));
+    uint8_t *d = o + q.header + q.ctl;
+    const Plan &p = c->plan;
+    CU(cudaMemcpyAsync(d, p.regs[0], q.regs, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(d + q.regs, p.regs[1], q.regs, cudaMemcpyDeviceToHost, c->stream));
+    d += 2 * q.regs;
+    CU(cudaMemcpyAsync(d, p.F[0], q.bits, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(d + q.bits, p.F[1], q.bits, cudaMemcpyDeviceToHost, c->stream));
+    d += 2 * q.bits;
+    CU(cudaMemcpyAsync(d, p.hist, q.hist, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(d + q.hist, p.blk_part, q.blk, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return HANF_OK;
+}
+
+int hanf_checkpoint_load(hanf_ctx *c, const void *buf, size_t bytes)
+{
+    if (!c || !buf) return fail(HANF_EINVAL, "NULL argument");
+    const CkpParts q = ckp_parts(c);
+    if (bytes < q.total) return fail(HANF_EINVAL, "checkpoint of %zu bytes, %zu expected", bytes, q.total);
+    const uint8_t *in = static_cast<const uint8_t *>(buf);
+    CkpHeader h;
+    std::memcpy(&h, in, sizeof h);
+    const CkpHeader mine = ckp_header(c);
+    if (std::memcmp(&h, &mine, sizeof h) != 0)
+        return fail(HANF_EINVAL, "checkpoint belongs to another graph, layout or seed set");
+    DevCtl ctl;
+    std::memcpy(&ctl, in + q.header, sizeof ctl);
+    const uint8_t *d = in + q.header + q.ctl;
+    const Plan &p = c->plan;
+    CU(cudaMemcpyAsync(p.ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.regs[0], d, q.regs, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.regs[1], d + q.regs, q.regs, cudaMemcpyHostToDevice, c->stream));
+    d += 2 * q.regs;
+    CU(cudaMemcpyAsync(p.F[0], d, q.bits, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.F[1], d + q.bits, q.bits, cudaMemcpyHostToDevice, c->stream));
+    d += 2 * q.bits;
+    CU(cudaMemcpyAsync(p.hist, d, q.hist, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.blk_part, d + q.hist, q.blk, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->host_ctl = ctl;
+    return HANF_OK;
+}
+
+int hanf_ed_interval(const double *N, int32_t T, double alpha, double eps, int32_t *lo,
+                     int32_t *hi)
+{
+    if (!N || !lo || !hi || T < 0 || eps < 0) return fail(HANF_EINVAL, "bad argument");
+    double M = N[0];
+    for (int t = 1; t <= T; ++t) M = std::max(M, N[t]);
+    *lo = -1;
+    *hi = -1;
+    for (int t = 0; t <= T; ++t) {
+        const double H = N[t] / M;
+        if (H <= alpha * (1.0 - 2.0 * eps)) *lo = t;
+        if (*hi < 0 && H >= alpha * (1.0 + 2.0 * eps)) *hi = t;
+    }
+    return HANF_OK;
+}
+
+int hanf_stats_runs(const double *N, int32_t R, int32_t cap, const int32_t *T, double alpha,
+                    int32_t exclude_zero, double *out10)
+{
+    if (!N || !T || !out10 || R < 1 || cap < 1) return fail(HANF_EINVAL, "bad argument");
+    double sum[5] = {0, 0, 0, 0, 0}, sq[5] = {0, 0, 0, 0, 0};
+    for (int r = 0; r < R; ++r) {
+        if (T[r] < 0 || T[r] >= cap) return fail(HANF_EINVAL, "T[%d] outside 0..cap-1", r);
+        double s5[5];
+        const int rc = hanf_stats(N + (size_t)r * cap, T[r], alpha, exclude_zero, s5);
+        if (rc) return rc;
+        for (int k = 0; k < 5; ++k) {
+            sum[k] += s5[k];
+            sq[k] += s5[k] * s5[k];
+        }
+    }
+    for (int k = 0; k < 5; ++k) {
+        const double mean = sum[k] / R;
+        out10[k] = mean;
+        out10[5 + k] = R > 1 ? std::sqrt(std::max(0.0, (sq[k] - R * mean * mean) / (R - 1))) : 0.0;
+    }
     return HANF_OK;
 }
 

@@ -23,7 +23,9 @@ FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 # Every function declared in include/hanf.h.
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
            "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
-           "hanf_trace", "hanf_stats", "hanf_estimate_static", "hanf_autotune",
+           "hanf_trace", "hanf_checkpoint_size", "hanf_checkpoint_save", "hanf_checkpoint_load",
+           "hanf_continue", "hanf_stats", "hanf_ed_interval", "hanf_stats_runs",
+           "hanf_estimate_static", "hanf_autotune",
            "hanf_server_create",
            "hanf_server_submit", "hanf_server_wait", "hanf_server_cancel", "hanf_server_stats",
            "hanf_server_destroy", "hanf_destroy", "hanf_last_error")
@@ -100,6 +102,20 @@ def lib():
         L.hanf_stats.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _i32, ctypes.POINTER(_f64)]
         L.hanf_estimate_static.restype = _i32
         L.hanf_estimate_static.argtypes = [_vp, _i64, _i32, _i32, _vp, _vp]
+        L.hanf_checkpoint_size.restype = _i32
+        L.hanf_checkpoint_size.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.hanf_checkpoint_save.restype = _i32
+        L.hanf_checkpoint_save.argtypes = [_vp, _vp, ctypes.c_size_t]
+        L.hanf_checkpoint_load.restype = _i32
+        L.hanf_checkpoint_load.argtypes = [_vp, _vp, ctypes.c_size_t]
+        L.hanf_continue.restype = _i32
+        L.hanf_continue.argtypes = [_vp, _i32, ctypes.POINTER(_f64), _i32, ctypes.POINTER(_i32)]
+        L.hanf_ed_interval.restype = _i32
+        L.hanf_ed_interval.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _f64,
+                                       ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+        L.hanf_stats_runs.restype = _i32
+        L.hanf_stats_runs.argtypes = [ctypes.POINTER(_f64), _i32, _i32, ctypes.POINTER(_i32), _f64,
+                                      _i32, ctypes.POINTER(_f64)]
         L.hanf_autotune.restype = _i32
         L.hanf_autotune.argtypes = [_i64, _i64, _vp, _vp, _i32, _i32, _u64, ctypes.POINTER(Opts),
                                     _vp, ctypes.c_size_t, ctypes.c_char_p, ctypes.POINTER(Opts),
@@ -191,6 +207,32 @@ def estimate_static(regs, n: int, log2m: int, runs: int, out, stream=None) -> No
                                      out.data_ptr(), stream.cuda_stream))
 
 
+def ed_interval(N, alpha=0.9, eps=0.0):
+    """Algorithm 3: (D-, D+) bracketing the effective diameter (-1 = none)."""
+    N = np.ascontiguousarray(N, dtype=np.float64)
+    lo, hi = _i32(), _i32()
+    check(lib().hanf_ed_interval(N.ctypes.data_as(ctypes.POINTER(_f64)), N.size - 1, alpha, eps,
+                                 ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def stats_runs(N_runs, alpha=0.9, exclude_zero=False) -> dict:
+    """Mean and standard deviation over runs of ed, ied, mean, var, spid."""
+    R = len(N_runs)
+    cap = max(len(x) for x in N_runs)
+    N = np.zeros((R, cap), dtype=np.float64)
+    T = np.zeros(R, dtype=np.int32)
+    for r, x in enumerate(N_runs):
+        N[r, :len(x)] = x
+        T[r] = len(x) - 1
+    out = np.zeros(10, dtype=np.float64)
+    check(lib().hanf_stats_runs(N.ctypes.data_as(ctypes.POINTER(_f64)), R, cap,
+                                T.ctypes.data_as(ctypes.POINTER(_i32)), alpha, int(exclude_zero),
+                                out.ctypes.data_as(ctypes.POINTER(_f64))))
+    keys = ("ed", "ied", "mean", "var", "spid")
+    return {k: (out[i], out[5 + i]) for i, k in enumerate(keys)}
+
+
 class HyperANF:
     """One HyperANF context (Algorithm 2 over R seeded runs) on a CUDA device.
 
@@ -265,6 +307,26 @@ class HyperANF:
         """hanf_run into caller-provided arrays; returns the status code."""
         return lib().hanf_run(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)),
                               N.shape[1], T.ctypes.data_as(ctypes.POINTER(_i32)))
+
+    def checkpoint(self) -> np.ndarray:
+        """The state after the last pass as a host byte array."""
+        size = ctypes.c_size_t()
+        check(lib().hanf_checkpoint_size(self._ctx, ctypes.byref(size)))
+        buf = np.empty(size.value, dtype=np.uint8)
+        check(lib().hanf_checkpoint_save(self._ctx, buf.ctypes.data, size.value))
+        return buf
+
+    def restore(self, buf: np.ndarray) -> None:
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(lib().hanf_checkpoint_load(self._ctx, buf.ctypes.data, buf.size))
+
+    def resume(self, max_iter: int = 4096, cap: int = 4096):
+        """Passes from the current state to stabilisation (hanf_continue)."""
+        N = np.zeros((self.R, cap), dtype=np.float64)
+        T = np.zeros(self.R, dtype=np.int32)
+        check(lib().hanf_continue(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)), cap,
+                                  T.ctypes.data_as(ctypes.POINTER(_i32))))
+        return [N[r, :T[r] + 1].copy() for r in range(self.R)], T
 
     def registers(self, run: int = 0, first: int = 0, count: int | None = None) -> np.ndarray:
         count = self.n - first if count is None else count

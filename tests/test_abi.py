@@ -79,3 +79,16 @@ def test_stats_match_oracle(H, oracle):
                     assert math.isnan(a[k])
                 else:
                     assert a[k] == pytest.approx(b[k], rel=1e-13, abs=1e-13)
+
+
+def test_ed_interval_and_run_stats_match_oracle(H, oracle):
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        N = np.cumsum(rng.uniform(1, 100, rng.integers(1, 25)))
+        for eps in (0.0, 0.01, 0.1):
+            assert H.ed_interval(N, 0.9, eps) == oracle.ed_interval(N, 0.9, eps)
+    runs = [np.cumsum(rng.uniform(1, 50, rng.integers(2, 15))) for _ in range(7)]
+    a, b = H.stats_runs(runs), oracle.stats_runs(runs)
+    for k in a:
+        assert a[k][0] == pytest.approx(b[k][0], rel=1e-12)
+        assert a[k][1] == pytest.approx(b[k][1], rel=1e-9, abs=1e-12)

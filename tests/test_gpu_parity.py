@@ -267,3 +267,46 @@ def test_bit_sliced_layout_rejects_unsupported(H):
         with pytest.raises(H.HanfError) as e:
             H.HyperANF(off, tgt, log2m, **kw)
         assert e.value.code == H.HANF_EINVAL
+
+
+
+@pytest.mark.parametrize("layout,R", [("byte", 1), ("byte", 4), ("packed", 1)])
+def test_checkpoint_resume_bit_identical(H, layout, R, tmp_path):
+    """Save after some passes, load into a fresh context, resume: counters, T
+    and N(t) equal those of an uninterrupted run."""
+    off, tgt = G.rmat(12, seed=17)
+    kw = dict(runs=R, layout=layout)
+    with H.HyperANF(off, tgt, 6, SEED, **kw) as h:
+        N_ref, T_ref = h.run()
+        regs_ref = [h.registers(r) for r in range(R)]
+    for stop in (0, 1, 3):
+        with H.HyperANF(off, tgt, 6, SEED, **kw) as h:
+            for _ in range(stop):
+                h.iterate()
+            ckp = h.checkpoint()
+        path = tmp_path / f"ckp{stop}.bin"
+        ckp.tofile(path)
+        with H.HyperANF(off, tgt, 6, SEED, use_graph=(stop == 1), **kw) as h2:
+            h2.restore(np.fromfile(path, dtype=np.uint8))
+            assert h2.t == stop
+            N, T = h2.resume()
+            assert list(T) == list(T_ref)
+            for r in range(R):
+                assert np.array_equal(N[r], N_ref[r])
+                assert np.array_equal(h2.registers(r), regs_ref[r])
+
+
+def test_resume_after_pass_limit_and_mismatch(H):
+    off, tgt = G.path(40)
+    with H.HyperANF(off, tgt, 6, SEED) as h:
+        N_full, T_full = h.run()
+        Np = np.zeros((1, 4096))
+        Tp = np.zeros(1, dtype=np.int32)
+        assert h.run_raw(Np, Tp, max_iter=5) == H.HANF_ERANGE
+        N2, T2 = h.resume()
+        assert list(T2) == list(T_full) and np.array_equal(N2[0], N_full[0])
+        ckp = h.checkpoint()
+    with H.HyperANF(off, tgt, 6, SEED + 1) as other:
+        with pytest.raises(H.HanfError) as e:
+            other.restore(ckp)
+        assert e.value.code == H.HANF_EINVAL

@@ -370,3 +370,41 @@ def test_symmetric_final_sum_equals_algorithm2(oracle, name):
         seed = oracle.run_seed(SEED, s)
         N, T, _ = oracle.hyperanf(off, tgt, 6, seed)
         assert oracle.symmetric_final_sum(off, tgt, 6, seed) == pytest.approx(N[-1], rel=1e-14)
+
+
+# ---------------------------------------------------------------- Algorithm 3
+
+
+@pytest.mark.parametrize("n", [5, 12, 40])
+def test_ed_interval_exact_bracket(oracle, n):
+    """With exact N (eps = 0) Algorithm 3's upper end is the effective
+    diameter and the lower end the last t below alpha; a positive eps can only
+    widen the bracket."""
+    N = np.array([_path_nf(n, t) for t in range(n)], dtype=np.float64)
+    ed = oracle.stats(N)["ed"]
+    lo, hi = oracle.ed_interval(N, 0.9, 0.0)
+    assert hi == ed
+    M = N.max()
+    assert lo == max(t for t in range(n) if N[t] / M <= 0.9)
+    lo2, hi2 = oracle.ed_interval(N, 0.9, 0.02)
+    assert lo2 <= lo and (hi2 >= hi or hi2 == -1)
+
+
+@pytest.mark.parametrize("l", [2, 3])
+def test_ed_interval_clique_path(oracle, l):
+    """Section 4's graph: the bracket of the exact distribution is [l, l+1];
+    stopping one pass early puts the whole bracket at 1 or below."""
+    k = 2 * l * l + 5 * l + 2
+    exact = np.array([clique_path_nf(k, l, t) for t in range(l + 2)], dtype=np.float64)
+    assert oracle.ed_interval(exact, 0.9, 0.0) == (l, l + 1)
+    lo, hi = oracle.ed_interval(exact[: l + 1], 0.9, 0.0)
+    assert hi == 1
+
+
+def test_stats_runs_matches_per_run(oracle):
+    off, tgt = G.er(300, 900, seed=3)
+    runs = [oracle.hyperanf(off, tgt, 6, oracle.run_seed(SEED, r))[0] for r in range(6)]
+    agg = oracle.stats_runs(runs)
+    spids = [oracle.stats(N)["spid"] for N in runs]
+    assert agg["spid"][0] == pytest.approx(np.mean(spids))
+    assert agg["spid"][1] == pytest.approx(np.std(spids, ddof=1))
