@@ -87,6 +87,8 @@ typedef struct hanf_opts {
     int32_t layout;        /* 0 = one byte per register; 1 = five bit-planes of
                               m bits (5m/8 bytes per counter; runs = 1 and
                               m >= 32); results are identical               */
+    int32_t node_stats;    /* 1 = keep per-node statistics (hanf_node_stats,
+                              hanf_node_radius): 32 bytes per node and run    */
     const uint64_t *seeds; /* R explicit run seeds (host), or NULL             */
     void *stream;          /* cudaStream_t for every launch; NULL = default    */
 } hanf_opts;
@@ -272,6 +274,24 @@ HANF_API int hanf_checkpoint_save(hanf_ctx *ctx, void *buf, size_t bytes);
 HANF_API int hanf_checkpoint_load(hanf_ctx *ctx, const void *buf, size_t bytes);
 HANF_API int hanf_continue(hanf_ctx *ctx, int32_t max_iter, double *N_out, int32_t cap,
                            int32_t *T_out);
+
+/* Per-node statistics (opts.node_stats = 1) -- the radius distribution and
+ * closeness centrality that the paper's conclusion proposes to build with
+ * HyperANF.  For the last completed run and nodes [first, first+count) of
+ * run r (input ids), from the node's estimates E_v(0..T): reach = E_v(T)
+ * (nodes reachable from v, v included), dist = sum_t t (E_v(t) - E_v(t-1))
+ * (sum of distances to them; closeness = (reach - 1) / dist), ecc = the last
+ * t with E_v(t) != E_v(t-1) (eccentricity estimate; never above the true
+ * one).  Host outputs, each nullable.  Synchronises. */
+HANF_API int hanf_node_stats(hanf_ctx *ctx, int32_t run, int64_t first, int64_t count,
+                             double *reach, double *dist, int32_t *ecc);
+
+/* Effective radius of every node (HADI's radius at alpha, e.g. 0.9): the
+ * first t with E_v(t) >= alpha E_v(T).  Replays the whole of Algorithm 2 once
+ * (deterministic, same counters) after a completed run with node_stats = 1,
+ * then copies radius[0..count) of run r for input ids first.. to the host. */
+HANF_API int hanf_node_radius(hanf_ctx *ctx, double alpha, int32_t run, int64_t first,
+                              int64_t count, int32_t *radius);
 
 /* Algorithm 3 (Section 4, Corollary 2): with each N(t) known to relative
  * error eps, M = max_t N(t), *lo = the largest D- with N(D-)/M <= alpha(1-2eps)

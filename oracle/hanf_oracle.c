@@ -378,3 +378,51 @@ ORA_API void ora_ed_interval(const double *N, int32_t T, double alpha, double ep
     for (t = 0; t <= T; ++t)
         if (N[t] / M >= alpha * (1.0 + 2.0 * eps)) { *hi = t; break; }
 }
+
+/* Per-node statistics of the estimates E_v(t) = size(c_t[v]), t = 0..T, of
+ * one run of Algorithm 2 (the radius distribution and closeness centrality
+ * proposed in the paper's conclusion): reach = E_v(T); dist = sum over
+ * t = 1..T of t (E_v(t) - E_v(t-1)); ecc = the last t with
+ * E_v(t) != E_v(t-1) (0 if none); rad = the first t with
+ * E_v(t) >= alpha E_v(T).  Keeps every E_v(t): for small graphs.  Returns T,
+ * or -1 if cap passes were not enough, -2 on allocation failure. */
+ORA_API int32_t ora_node_stats(const int64_t *off, const int32_t *tgt, int64_t n, int32_t b,
+                               uint64_t seed, double alpha, int32_t cap, double *reach,
+                               double *dist, int32_t *ecc, int32_t *rad)
+{
+    int32_t m = 1 << b, t, T = -1;
+    size_t bytes = (size_t)(n ? n : 1) * (size_t)m;
+    uint8_t *c = (uint8_t *)malloc(bytes), *cn = (uint8_t *)malloc(bytes);
+    double *E = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)(n ? n : 1));
+    int64_t v;
+    if (!c || !cn || !E) { free(c); free(cn); free(E); return -2; }
+    ora_init(c, n, b, seed);
+    for (t = 0; t < cap; ++t) {
+        int64_t changed;
+        uint8_t *tmp;
+        for (v = 0; v < n; ++v) E[(size_t)t * n + v] = ora_size(c + v * m, m);
+        changed = ora_union_pass(off, tgt, n, m, c, cn, 1);
+        tmp = c; c = cn; cn = tmp;
+        if (changed == 0) { T = t; break; }
+    }
+    if (T >= 0) {
+        for (v = 0; v < n; ++v) {
+            double s = 0.0, last = E[(size_t)T * n + v];
+            int32_t e = 0, r = -1;
+            for (t = 0; t <= T; ++t) {
+                double Et = E[(size_t)t * n + v];
+                if (t > 0 && Et != E[(size_t)(t - 1) * n + v]) {
+                    s = s + (double)t * (Et - E[(size_t)(t - 1) * n + v]);
+                    e = t;
+                }
+                if (r < 0 && Et >= alpha * last) r = t;
+            }
+            reach[v] = last;
+            dist[v] = s;
+            ecc[v] = e;
+            rad[v] = r;
+        }
+    }
+    free(c); free(cn); free(E);
+    return T;
+}

@@ -88,6 +88,10 @@ def _load():
         lib.ora_ed_interval.restype = None
         lib.ora_ed_interval.argtypes = [_f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                         _i32p, _i32p]
+        lib.ora_node_stats.restype = ctypes.c_int32
+        lib.ora_node_stats.argtypes = [_i64p, _i32p, ctypes.c_int64, ctypes.c_int32,
+                                       ctypes.c_uint64, ctypes.c_double, ctypes.c_int32,
+                                       _f64p, _f64p, _i32p, _i32p]
         lib.ora_stats.restype = None
         lib.ora_stats.argtypes = [_f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                   _f64p]
@@ -250,3 +254,46 @@ def stats_runs(N_runs, alpha_: float = 0.9, exclude_zero: bool = False) -> dict:
         x = np.array([p[k] for p in per])
         out[k] = (float(x.mean()), float(x.std(ddof=1)) if len(x) > 1 else 0.0)
     return out
+
+
+def node_stats(offsets, targets, b: int, seed: int, alpha_: float = 0.9, cap: int = 512) -> dict:
+    """Per-node reach, distance sum, eccentricity and radius estimates."""
+    off, tgt, n = _csr(offsets, targets)
+    reach = np.zeros(max(n, 1))
+    dist = np.zeros(max(n, 1))
+    ecc = np.zeros(max(n, 1), dtype=np.int32)
+    rad = np.zeros(max(n, 1), dtype=np.int32)
+    T = _load().ora_node_stats(_p(off, _i64p), _p(tgt, _i32p), n, b, seed & (2**64 - 1), alpha_,
+                               cap, _p(reach, _f64p), _p(dist, _f64p), _p(ecc, _i32p),
+                               _p(rad, _i32p))
+    if T < 0:
+        raise RuntimeError(f"oracle node_stats failed ({T})")
+    return {"reach": reach[:n], "dist": dist[:n], "ecc": ecc[:n], "radius": rad[:n], "T": T}
+
+
+def exact_node_distances(offsets, targets):
+    """Exact per-node (reachable count, distance sum, eccentricity) by BFS."""
+    off = np.asarray(offsets, dtype=np.int64)
+    tgt = np.asarray(targets, dtype=np.int64)
+    n = off.size - 1
+    reach = np.zeros(n, dtype=np.int64)
+    dsum = np.zeros(n, dtype=np.int64)
+    ecc = np.zeros(n, dtype=np.int64)
+    for x in range(n):
+        dist = {x: 0}
+        frontier = [x]
+        d = 0
+        while frontier:
+            d += 1
+            nxt = []
+            for u in frontier:
+                for w in tgt[off[u]:off[u + 1]]:
+                    w = int(w)
+                    if w not in dist:
+                        dist[w] = d
+                        nxt.append(w)
+            frontier = nxt
+        reach[x] = len(dist)
+        dsum[x] = sum(dist.values())
+        ecc[x] = max(dist.values())
+    return reach, dsum, ecc

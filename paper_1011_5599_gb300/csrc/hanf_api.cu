@@ -76,7 +76,7 @@ struct Sizes {
     int64_t n, arcs;
     int32_t log2m, m, R, W, layout;
     int32_t d_small, d_hub, history;
-    bool copy_graph, transpose, relabel;
+    bool copy_graph, transpose, relabel, node_stats;
     int64_t nwords, nred, ntiles, max_hub, max_seg, scan_elems;
 };
 
@@ -85,6 +85,7 @@ struct Layout {
     size_t seg_node, seg_beg, seg_end, hub_first, hub_part, hub_any;
     size_t blk_part, red_part, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
     size_t seg_counts, seg_offs, totals, perm, inv, off2, tgt2, rcounts, roffs, stage;
+    size_t ns_prev, ns_dist, ns_reach, ns_ecc, ns_rad;
     size_t total;
 };
 
@@ -126,6 +127,7 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     s->copy_graph = copy_graph != 0;
     s->transpose = o.frontier == HANF_FRONTIER_AUTO;
     s->relabel = o.relabel != 0 && n > 0;
+    s->node_stats = o.node_stats != 0;
     s->nwords = std::max<int64_t>(1, (n + 63) / 64);
     s->nred = (s->nwords + hanf::kEstChunk - 1) / hanf::kEstChunk;
     s->ntiles = hanf::classify_blocks(n);
@@ -185,9 +187,17 @@ Layout make_layout(const Sizes &s)
         L.rcounts = take(8 * hanf::relabel_count_elems(s.n));
         L.roffs = take(8 * hanf::relabel_count_elems(s.n));
     }
-    if (s.relabel || s.layout)
+    if (s.node_stats) {
+        const size_t cells = rows * (size_t)s.R;
+        L.ns_prev = take(8 * cells);
+        L.ns_dist = take(8 * cells);
+        L.ns_reach = take(8 * cells);
+        L.ns_ecc = take(4 * cells);
+        L.ns_rad = take(4 * cells);
+    }
+    if (s.relabel || s.layout || s.node_stats)
         L.stage = take((size_t)std::min<int64_t>(std::max<int64_t>(s.n, 1), kStageRows) *
-                       std::max(s.W, s.m));
+                       std::max(std::max(s.W, s.m), 8));
     L.total = at;
     return L;
 }
@@ -340,6 +350,7 @@ void hanf_default_opts(hanf_opts *o)
     o->relabel = 1;
     o->gather_variant = 0;
     o->layout = 0;
+    o->node_stats = 0;
     o->seeds = nullptr;
     o->stream = nullptr;
 }
@@ -475,7 +486,15 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
         p.orig_id = inv;
         c->perm = perm;
     }
-    if (s.relabel || s.layout) c->stage = ws + L.stage;
+    if (s.relabel || s.layout || s.node_stats) c->stage = ws + L.stage;
+    if (s.node_stats) {
+        p.node_stats = 1;
+        p.ns_prev = reinterpret_cast<double *>(ws + L.ns_prev);
+        p.ns_dist = reinterpret_cast<double *>(ws + L.ns_dist);
+        p.ns_reach = reinterpret_cast<double *>(ws + L.ns_reach);
+        p.ns_ecc = reinterpret_cast<int32_t *>(ws + L.ns_ecc);
+        p.ns_rad = reinterpret_cast<int32_t *>(ws + L.ns_rad);
+    }
 
     // 2. degree classes -> [small | medium | hub] node lists
     int64_t tot[4] = {0, 0, 0, 0};
@@ -869,6 +888,72 @@ int hanf_checkpoint_load(hanf_ctx *c, const void *buf, size_t bytes)
     CU(cudaMemcpyAsync(p.blk_part, d + q.hist, q.blk, cudaMemcpyHostToDevice, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     c->host_ctl = ctl;
+    return HANF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Copy per-node values of run r, input ids first.., to the host in chunks.
+int copy_node_values(hanf_ctx *c, const void *src_all, int elem, int32_t run, int64_t first,
+                     int64_t count, void *out)
+{
+    const uint8_t *src = static_cast<const uint8_t *>(src_all) + (size_t)run * c->plan.n * elem;
+    for (int64_t i = 0; i < count; i += kStageRows) {
+        const int64_t k = std::min<int64_t>(kStageRows, count - i);
+        CU(hanf::launch_gather_node_values(src, c->perm, first + i, k, elem, c->stage, c->stream));
+        CU(cudaMemcpyAsync(static_cast<uint8_t *>(out) + (size_t)i * elem, c->stage, (size_t)k * elem,
+                           cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return HANF_OK;
+}
+
+int check_node_range(hanf_ctx *c, int32_t run, int64_t first, int64_t count)
+{
+    if (!c) return fail(HANF_EINVAL, "NULL context");
+    if (!c->plan.node_stats) return fail(HANF_ESTATE, "context created without node_stats");
+    if (run < 0 || run >= c->plan.R) return fail(HANF_EINVAL, "run %d out of range", run);
+    if (first < 0 || count < 0 || first + count > c->plan.n)
+        return fail(HANF_EINVAL, "node range out of bounds");
+    return HANF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hanf_node_stats(hanf_ctx *c, int32_t run, int64_t first, int64_t count, double *reach,
+                    double *dist, int32_t *ecc)
+{
+    int rc = check_node_range(c, run, first, count);
+    if (rc) return rc;
+    if (reach && (rc = copy_node_values(c, c->plan.ns_prev, 8, run, first, count, reach))) return rc;
+    if (dist && (rc = copy_node_values(c, c->plan.ns_dist, 8, run, first, count, dist))) return rc;
+    if (ecc && (rc = copy_node_values(c, c->plan.ns_ecc, 4, run, first, count, ecc))) return rc;
+    return HANF_OK;
+}
+
+int hanf_node_radius(hanf_ctx *c, double alpha, int32_t run, int64_t first, int64_t count,
+                     int32_t *radius)
+{
+    int rc = check_node_range(c, run, first, count);
+    if (rc) return rc;
+    rc = read_ctl(c);
+    if (rc) return rc;
+    if (!c->host_ctl.done || c->host_ctl.err) return fail(HANF_ESTATE, "no completed run to replay");
+    Plan &p = c->plan;
+    const size_t cells = (size_t)std::max<int64_t>(p.n, 1) * p.R;
+    CU(cudaMemcpyAsync(p.ns_reach, p.ns_prev, 8 * cells, cudaMemcpyDeviceToDevice, c->stream));
+    const int32_t T = c->host_ctl.t;
+    p.ns_radius_mode = 1;
+    p.ns_alpha = alpha;
+    rc = reset(c, std::max<int32_t>(T + 1, 1));
+    while (rc == HANF_OK && !c->host_ctl.done) rc = one_pass(c);
+    p.ns_radius_mode = 0;
+    if (rc) return rc;
+    if (radius) return copy_node_values(c, p.ns_rad, 4, run, first, count, radius);
     return HANF_OK;
 }
 

@@ -71,6 +71,14 @@ struct Plan {
     double amm;                       // alpha_m m^2
     const uint64_t *seeds;            // R run seeds
     const int32_t *orig_id;           // input id of every stored node (null: identity)
+    // per-node statistics of the E_v(t) sequence, [run][node] (node_stats)
+    double *ns_prev;                  // E_v at the last estimate
+    double *ns_dist;                  // sum_t t (E_v(t) - E_v(t-1))
+    double *ns_reach;                 // E_v(T) of the previous run (radius replay)
+    int32_t *ns_ecc;                  // last t with E_v(t) != E_v(t-1)
+    int32_t *ns_rad;                  // first t with E_v(t) >= ns_alpha E_v(T)
+    double ns_alpha;
+    int32_t node_stats, ns_radius_mode;
     int32_t frontier, push_den, dense_den;
     int32_t history_cap;
     int32_t union_warps;              // resident warps of the union launch
@@ -113,6 +121,8 @@ cudaError_t launch_relabel(const int64_t *off, const int32_t *tgt, int64_t n, in
 int64_t relabel_count_elems(int64_t n);
 cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
                                int64_t count, int W, uint8_t *out, cudaStream_t s);
+cudaError_t launch_gather_node_values(const void *src, const int32_t *perm, int64_t first,
+                                      int64_t count, int elem_bytes, void *out, cudaStream_t s);
 cudaError_t launch_unpack_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
                                int64_t count, int m, uint8_t *out, cudaStream_t s);
 

@@ -781,6 +781,37 @@ __device__ __forceinline__ double node_size(const Plan &p, const uint8_t *rc, in
     return E;
 }
 
+// Per-node statistics of the sequence E_v(0..T) (the radius distribution and
+// closeness centrality of the paper's conclusion): reach E_v(T), the distance
+// sum sum_t t (E_v(t) - E_v(t-1)), the last t at which E_v changed, and in a
+// replay the first t with E_v(t) >= alpha E_v(T).  Products and sums are
+// rounded one by one (no fused multiply-add), as the oracle computes them.
+__device__ __forceinline__ void node_stats_update(const Plan &p, int r, int64_t v, double E,
+                                                  bool all, int t)
+{
+    const int64_t i = (int64_t)r * p.n + v;
+    if (all) {
+        p.ns_prev[i] = E;
+        if (p.ns_radius_mode) {
+            p.ns_rad[i] = E >= __dmul_rn(p.ns_alpha, p.ns_reach[i]) ? 0 : -1;
+        } else {
+            p.ns_dist[i] = 0.0;
+            p.ns_ecc[i] = 0;
+        }
+        return;
+    }
+    const double d = __dsub_rn(E, p.ns_prev[i]);
+    if (d != 0.0) {
+        if (!p.ns_radius_mode) {
+            p.ns_dist[i] = __dadd_rn(p.ns_dist[i], __dmul_rn((double)t, d));
+            p.ns_ecc[i] = t;
+        }
+        p.ns_prev[i] = E;
+    }
+    if (p.ns_radius_mode && p.ns_rad[i] < 0 && E >= __dmul_rn(p.ns_alpha, p.ns_reach[i]))
+        p.ns_rad[i] = t;
+}
+
 // Per 64-node block and run: sum of size() over the block, recomputed only
 // for blocks with a counter changed by the last pass (Section 3.3, harmonic
 // partial sums of small blocks).  A warp per (run, block); the warp sum uses
@@ -815,6 +846,10 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
         }
         const double e0 = v0 < p.n ? node_size(p, rc, v0, r) : 0.0;
         const double e1 = v1 < p.n ? node_size(p, rc, v1, r) : 0.0;
+        if (p.node_stats) {
+            if (v0 < p.n) node_stats_update(p, r, v0, e0, all, c->t);
+            if (v1 < p.n) node_stats_update(p, r, v1, e1, all, c->t);
+        }
         double s = e0 + e1;
 #pragma unroll
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -1175,6 +1210,16 @@ __global__ void k_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t 
         const int64_t row = perm ? perm[first + i] : first + i;
         reinterpret_cast<uint4 *>(out)[c] = reinterpret_cast<const uint4 *>(regs)[row * cpr + j];
     }
+}
+
+// Per-node values of input ids first..first+count (through the relabelling).
+template <typename V>
+__global__ void k_gather_vals(const V *src, const int32_t *perm, int64_t first, int64_t count,
+                              V *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src[perm ? perm[first + i] : first + i];
 }
 
 int grid_for(int64_t work, int per_block, int64_t cap = 152 * 32)
@@ -1540,8 +1585,13 @@ __global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
             for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
             if (lane == 0 && d) atomicAdd(&p.ctl->changed_in_arcs, d);
         }
-        double s = (v0 < p.n ? pnode_size<P>(p, rc, v0) : 0.0) +
-                   (v1 < p.n ? pnode_size<P>(p, rc, v1) : 0.0);
+        const double e0 = v0 < p.n ? pnode_size<P>(p, rc, v0) : 0.0;
+        const double e1 = v1 < p.n ? pnode_size<P>(p, rc, v1) : 0.0;
+        if (p.node_stats) {
+            if (v0 < p.n) node_stats_update(p, 0, v0, e0, all, c->t);
+            if (v1 < p.n) node_stats_update(p, 0, v1, e1, all, c->t);
+        }
+        double s = e0 + e1;
 #pragma unroll
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0) p.blk_part[blk] = s;
@@ -1904,6 +1954,20 @@ cudaError_t launch_relabel(const int64_t *off, const int32_t *tgt, int64_t n, in
 }
 
 int64_t relabel_count_elems(int64_t n) { return kHotClasses * classify_blocks(n) + 1; }
+
+cudaError_t launch_gather_node_values(const void *src, const int32_t *perm, int64_t first,
+                                      int64_t count, int elem_bytes, void *out, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    if (elem_bytes == 8)
+        k_gather_vals<unsigned long long><<<grid_for(count, kBlock), kBlock, 0, s>>>(
+            static_cast<const unsigned long long *>(src), perm, first, count,
+            static_cast<unsigned long long *>(out));
+    else
+        k_gather_vals<uint32_t><<<grid_for(count, kBlock), kBlock, 0, s>>>(
+            static_cast<const uint32_t *>(src), perm, first, count, static_cast<uint32_t *>(out));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_unpack_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
                                int64_t count, int m, uint8_t *out, cudaStream_t s)

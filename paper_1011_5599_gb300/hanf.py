@@ -24,7 +24,8 @@ FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
            "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
            "hanf_trace", "hanf_checkpoint_size", "hanf_checkpoint_save", "hanf_checkpoint_load",
-           "hanf_continue", "hanf_stats", "hanf_ed_interval", "hanf_stats_runs",
+           "hanf_continue", "hanf_node_stats", "hanf_node_radius", "hanf_stats",
+           "hanf_ed_interval", "hanf_stats_runs",
            "hanf_estimate_static", "hanf_autotune",
            "hanf_server_create",
            "hanf_server_submit", "hanf_server_wait", "hanf_server_cancel", "hanf_server_stats",
@@ -57,6 +58,7 @@ class Opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("dense_den", ctypes.c_int32), ("relabel", ctypes.c_int32),
                 ("gather_variant", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("node_stats", ctypes.c_int32),
                 ("seeds", ctypes.POINTER(ctypes.c_uint64)), ("stream", ctypes.c_void_p)]
 
 
@@ -110,6 +112,10 @@ def lib():
         L.hanf_checkpoint_load.argtypes = [_vp, _vp, ctypes.c_size_t]
         L.hanf_continue.restype = _i32
         L.hanf_continue.argtypes = [_vp, _i32, ctypes.POINTER(_f64), _i32, ctypes.POINTER(_i32)]
+        L.hanf_node_stats.restype = _i32
+        L.hanf_node_stats.argtypes = [_vp, _i32, _i64, _i64, _vp, _vp, _vp]
+        L.hanf_node_radius.restype = _i32
+        L.hanf_node_radius.argtypes = [_vp, _f64, _i32, _i64, _i64, _vp]
         L.hanf_ed_interval.restype = _i32
         L.hanf_ed_interval.argtypes = [ctypes.POINTER(_f64), _i32, _f64, _f64,
                                        ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
@@ -155,7 +161,7 @@ def default_opts() -> Opts:
 
 def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=0,
               history_cap=0, use_graph=False, profile=False, seeds=None, stream=None,
-              dense_den=0, relabel=True, gather_variant=0, layout=0):
+              dense_den=0, relabel=True, gather_variant=0, layout=0, node_stats=False):
     o = default_opts()
     o.runs = runs
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
@@ -168,6 +174,7 @@ def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=
     o.dense_den = dense_den
     o.relabel = int(bool(relabel))
     o.gather_variant = gather_variant
+    o.node_stats = int(bool(node_stats))
     o.layout = {"byte": 0, "packed": 1}.get(layout, layout) if isinstance(layout, str) else layout
     keep = None
     if seeds is not None:
@@ -245,7 +252,7 @@ class HyperANF:
                  hub_min_deg: int = 0, history_cap: int = 0, use_graph: bool = False,
                  profile: bool = False, seeds=None, device=None, stream=None,
                  dense_den: int = 0, relabel: bool = True, gather_variant: int = 0,
-                 layout=0):
+                 layout=0, node_stats: bool = False):
         import torch
 
         self.device = torch.device(device if device is not None else "cuda")
@@ -273,7 +280,7 @@ class HyperANF:
         self._opts, self._seed_keep = make_opts(runs, frontier, push_den, small_max_deg,
                                                 hub_min_deg, history_cap, use_graph, profile,
                                                 seeds, self.stream.cuda_stream, dense_den,
-                                                relabel, gather_variant, layout)
+                                                relabel, gather_variant, layout, node_stats)
         size = workspace_size(n, arcs, log2m, self._opts, not on_dev)
         self.workspace_bytes = size
         with torch.cuda.device(self.device):
@@ -327,6 +334,24 @@ class HyperANF:
         check(lib().hanf_continue(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)), cap,
                                   T.ctypes.data_as(ctypes.POINTER(_i32))))
         return [N[r, :T[r] + 1].copy() for r in range(self.R)], T
+
+    def node_stats(self, run: int = 0, first: int = 0, count: int | None = None) -> dict:
+        """reach E_v(T), distance sum and eccentricity estimate per node."""
+        count = self.n - first if count is None else count
+        reach = np.zeros(max(count, 1))
+        dist = np.zeros(max(count, 1))
+        ecc = np.zeros(max(count, 1), dtype=np.int32)
+        check(lib().hanf_node_stats(self._ctx, run, first, count, reach.ctypes.data,
+                                    dist.ctypes.data, ecc.ctypes.data))
+        return {"reach": reach[:count], "dist": dist[:count], "ecc": ecc[:count]}
+
+    def node_radius(self, alpha: float = 0.9, run: int = 0, first: int = 0,
+                    count: int | None = None) -> np.ndarray:
+        """First t with E_v(t) >= alpha E_v(T) (replays the run once)."""
+        count = self.n - first if count is None else count
+        rad = np.zeros(max(count, 1), dtype=np.int32)
+        check(lib().hanf_node_radius(self._ctx, alpha, run, first, count, rad.ctypes.data))
+        return rad[:count]
 
     def registers(self, run: int = 0, first: int = 0, count: int | None = None) -> np.ndarray:
         count = self.n - first if count is None else count

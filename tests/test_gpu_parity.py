@@ -310,3 +310,25 @@ def test_resume_after_pass_limit_and_mismatch(H):
         with pytest.raises(H.HanfError) as e:
             other.restore(ckp)
         assert e.value.code == H.HANF_EINVAL
+
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(relabel=False), dict(runs=2), dict(layout="packed"),
+                                dict(use_graph=True, frontier="pull")])
+def test_node_statistics_match_oracle(H, oracle, kw):
+    """Per-node reach, distance sum, eccentricity and effective radius equal
+    the oracle's, computed from its own E_v(t) sequence."""
+    off, tgt = G.er(2000, 7000, seed=18)
+    R = kw.get("runs", 1)
+    with H.HyperANF(off, tgt, 6, SEED, node_stats=True, **kw) as h:
+        h.run()
+        got = [h.node_stats(r) for r in range(R)]
+        rad = [h.node_radius(0.9, r) for r in range(R)]
+        sub = h.node_stats(0, 100, 50)
+    for r in range(R):
+        ref = oracle.node_stats(off, tgt, 6, oracle.run_seed(SEED, r), 0.9)
+        assert np.array_equal(got[r]["reach"], ref["reach"])
+        assert np.array_equal(got[r]["dist"], ref["dist"])
+        assert np.array_equal(got[r]["ecc"], ref["ecc"])
+        assert np.array_equal(rad[r], ref["radius"])
+    assert np.array_equal(sub["dist"], got[0]["dist"][100:150])

@@ -408,3 +408,44 @@ def test_stats_runs_matches_per_run(oracle):
     spids = [oracle.stats(N)["spid"] for N in runs]
     assert agg["spid"][0] == pytest.approx(np.mean(spids))
     assert agg["spid"][1] == pytest.approx(np.std(spids, ddof=1))
+
+
+# ---------------------------------------------------------------- per-node statistics
+
+
+def test_node_eccentricity_never_exceeds_the_true_one(oracle):
+    """A counter can only change while its ball still grows, so the estimated
+    eccentricity is at most the exact one.  The last step often adds a node or
+    two whose hashes raise no register, so the two agree only part of the time."""
+    off, tgt = G.er(200, 500, seed=8)
+    reach, dsum, ecc = oracle.exact_node_distances(off, tgt)
+    agree = 0
+    for s in range(5):
+        st = oracle.node_stats(off, tgt, 8, oracle.run_seed(SEED, s))
+        assert np.all(st["ecc"] <= ecc)
+        agree += np.mean(st["ecc"] == ecc)
+    assert agree / 5 > 0.5
+
+
+def test_node_distance_sums_estimate_the_exact_ones(oracle):
+    """Averaged over seeds, reach and distance sums are within the
+    HyperLogLog error of the exact BFS values; the effective radius of the
+    path's first node is the smallest t covering 90% of its n nodes."""
+    off, tgt = G.er(300, 1200, seed=9)
+    reach, dsum, ecc = oracle.exact_node_distances(off, tgt)
+    S = 40
+    r_est = np.zeros(reach.size)
+    d_est = np.zeros(reach.size)
+    for s in range(S):
+        st = oracle.node_stats(off, tgt, 8, oracle.run_seed(SEED, s))
+        r_est += st["reach"] / S
+        d_est += st["dist"] / S
+    eta = 1.06 / 16
+    live = reach > 50
+    assert abs(np.mean(r_est[live] / reach[live]) - 1) < 3 * eta / np.sqrt(S) + 0.01
+    assert abs(np.mean(d_est[live] / dsum[live]) - 1) < 3 * eta / np.sqrt(S) + 0.03
+    # path of n nodes, node 0: ball of radius t holds t+1 nodes exactly
+    n = 30
+    rad = np.array([oracle.node_stats(*G.path(n), 8, oracle.run_seed(SEED, s))["radius"][0]
+                    for s in range(20)])
+    assert abs(np.median(rad) - (int(np.ceil(0.9 * n)) - 1)) <= 2
