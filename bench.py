@@ -450,15 +450,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        t = torch.tensor([elapsed, merges], dtype=torch.float64, device=device)
-        tmax = t[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t[1:].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        elapsed_all, merges_all = float(tmax.item()), float(tsum.item())
-    else:
-        elapsed_all, merges_all = elapsed, float(merges)
+    from paper_1011_5599_gb300.replicas import reduce_max_sum
+    elapsed_all, merges_all = reduce_max_sum(elapsed, merges, device=device)
     value = merges_all / elapsed_all
     if args.trace and args.driver == "host":
         h.run()
@@ -498,13 +491,7 @@ def main():
                 d2h += sum(x.nbytes for x in Ne)
         torch.cuda.synchronize()
         e_el = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([e_el], dtype=torch.float64, device=device)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_el = float(tt.item())
-            mm = torch.tensor([float(e_merges)], dtype=torch.float64, device=device)
-            dist.all_reduce(mm, op=dist.ReduceOp.SUM)
-            e_merges = float(mm.item())
+        e_el, e_merges = reduce_max_sum(e_el, e_merges, device=device)
         e2e = {"value": e_merges / e_el, "unit": UNIT,
                "h2d_bytes_per_step": int((n + 1) * 8 + arcs * 4),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps),
