@@ -19,6 +19,9 @@
  *   - Hash: h(v) = splitmix64(v XOR seed_r), seed_r = splitmix64(seed + r)
  *     unless explicit seeds are given; the register index is the top log2m
  *     bits of h, rho+ counts the leading zeroes of the remaining bits plus one.
+ *   - A context holds K >= 1 graphs (a batch, hanf_opts.num_graphs) and R runs
+ *     of each: S = K * R "slots", slot = graph * R + run; per-run outputs
+ *     (N(t), T) have one entry per slot.
  *   - size(): E = alpha_m m^2 / sum_j 2^-M[j] with the published alpha_m, and
  *     small-range linear counting E = m ln(m/V) when E <= 5m/2 and V > 0.
  *   - Device memory is never allocated by the library: the caller passes one
@@ -89,7 +92,17 @@ typedef struct hanf_opts {
                               m >= 32); results are identical               */
     int32_t node_stats;    /* 1 = keep per-node statistics (hanf_node_stats,
                               hanf_node_radius): 32 bytes per node and run    */
-    const uint64_t *seeds; /* R explicit run seeds (host), or NULL             */
+    int32_t num_graphs;    /* K >= 1 graphs batched in one context (0 = 1)    */
+    const int64_t *graph_base;  /* K > 1: K+1 node offsets (host); graph g owns
+                              stored nodes [base[g], base[g+1]); every base[g],
+                              g < K, a multiple of 64, base[K] = n             */
+    const int64_t *graph_nodes; /* K > 1: K node counts; nodes base[g] ..
+                              base[g]+nodes[g]-1 are graph g's nodes 0..; the
+                              rest of the range is padding without arcs; arcs
+                              stay inside their graph (checked)               */
+    const uint64_t *graph_seeds;/* K > 1: run r of graph g hashes with
+                              splitmix64(graph_seeds[g] + r); NULL = seed      */
+    const uint64_t *seeds; /* R explicit run seeds (host, K = 1), or NULL     */
     void *stream;          /* cudaStream_t for every launch; NULL = default    */
 } hanf_opts;
 
@@ -118,8 +131,8 @@ HANF_API int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t 
                 uint64_t seed, const hanf_opts *opts, void *workspace,
                 size_t workspace_bytes);
 
-/* Algorithm 2, the sum s = sum_v size(c[v]) at the current t, for every run:
- * N_out (host) receives R doubles.  Synchronises the stream. */
+/* Algorithm 2, the sum s = sum_v size(c[v]) at the current t, for every slot:
+ * N_out (host) receives S = K * R doubles.  Synchronises the stream. */
 HANF_API int hanf_estimate(hanf_ctx *ctx, double *N_out);
 
 /* One pass of Algorithm 2's main loop (t -> t+1): every counter becomes the
@@ -130,10 +143,10 @@ HANF_API int hanf_iterate(hanf_ctx *ctx, int64_t *changed_out);
 
 /* The whole of Algorithm 2: re-initialise, then print N(t) and run passes
  * until a pass changes no counter of any run (or max_iter passes ran).
- *   N_out (host): R x cap doubles, row r holds N_r(0..T_r) (later entries
- *     repeat N_r(T_r) up to the global T).
- *   T_out (host): R ints, T_r = the first pass index that changed no counter
- *     of run r.
+ *   N_out (host): S x cap doubles (S = K * R slots), row s holds N_s(0..T_s)
+ *     (later entries repeat N_s(T_s) up to the global T).
+ *   T_out (host): S ints, T_s = the first pass index that changed no counter
+ *     of slot s.
  * Returns HANF_ERANGE if stabilisation needs more than cap values or
  * max_iter passes (N_out then holds what was computed). */
 HANF_API int hanf_run(hanf_ctx *ctx, int32_t max_iter, double *N_out, int32_t cap, int32_t *T_out);

@@ -74,7 +74,7 @@ double hll_alpha(int m)
 
 struct Sizes {
     int64_t n, arcs;
-    int32_t log2m, m, R, W, layout;
+    int32_t log2m, m, R, W, layout, K, S;
     int32_t d_small, d_hub, history;
     bool copy_graph, transpose, relabel, node_stats;
     int64_t nwords, nred, ntiles, max_hub, max_seg, scan_elems;
@@ -86,6 +86,7 @@ struct Layout {
     size_t blk_part, red_part, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
     size_t seg_counts, seg_offs, totals, perm, inv, off2, tgt2, rcounts, roffs, stage;
     size_t ns_prev, ns_dist, ns_reach, ns_ecc, ns_rad;
+    size_t slot_T, slot_changed, blk_graph, g_base, g_nodes;
     size_t total;
 };
 
@@ -126,7 +127,21 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     s->history = o.history_cap ? o.history_cap : kDefaultHistory;
     s->copy_graph = copy_graph != 0;
     s->transpose = o.frontier == HANF_FRONTIER_AUTO;
-    s->relabel = o.relabel != 0 && n > 0;
+    s->K = o.num_graphs ? o.num_graphs : 1;
+    if (s->K < 1) return fail(HANF_EINVAL, "num_graphs=%d < 1", o.num_graphs);
+    if (s->K > 1) {
+        if (!o.graph_base || !o.graph_nodes) return fail(HANF_EINVAL, "batch tables are NULL");
+        if (o.graph_base[0] != 0 || o.graph_base[s->K] != n)
+            return fail(HANF_EINVAL, "graph_base must start at 0 and end at n");
+        for (int g = 0; g < s->K; ++g) {
+            if ((o.graph_base[g] & 63) != 0 || o.graph_base[g + 1] < o.graph_base[g])
+                return fail(HANF_EINVAL, "graph %d does not start at a multiple of 64", g);
+            if (o.graph_nodes[g] < 0 || o.graph_nodes[g] > o.graph_base[g + 1] - o.graph_base[g])
+                return fail(HANF_EINVAL, "graph %d has more nodes than its range", g);
+        }
+    }
+    s->S = s->K * s->R;
+    s->relabel = o.relabel != 0 && n > 0 && s->K == 1;
     s->node_stats = o.node_stats != 0;
     s->nwords = std::max<int64_t>(1, (n + 63) / 64);
     s->nred = (s->nwords + hanf::kEstChunk - 1) / hanf::kEstChunk;
@@ -169,9 +184,16 @@ Layout make_layout(const Sizes &s)
     L.hub_any = take(s.max_seg);
     L.blk_part = take(8 * s.nwords * s.R);
     L.red_part = take(8 * s.nred * s.R);
-    L.hist = take(8 * (size_t)s.history * s.R);
+    L.hist = take(8 * (size_t)s.history * s.S);
     L.lc = take(8 * (s.m + 1));
-    L.seeds = take(8 * s.R);
+    L.seeds = take(8 * (size_t)s.S);
+    L.slot_T = take(4 * (size_t)s.S);
+    L.slot_changed = take(8 * (size_t)s.S);
+    if (s.K > 1) {
+        L.blk_graph = take(4 * (size_t)s.nwords);
+        L.g_base = take(8 * (size_t)(s.K + 1));
+        L.g_nodes = take(8 * (size_t)s.K);
+    }
     L.ctl = take(sizeof(DevCtl));
     L.scan_tmp = take(8 * s.scan_elems);
     L.blk_counts = take(8 * (3 * s.ntiles + 1));
@@ -246,8 +268,8 @@ int reset(hanf_ctx *c, int32_t max_t)
     DevCtl h;
     std::memset(&h, 0, sizeof h);
     h.max_t = max_t;
-    for (int r = 0; r < hanf::kMaxRuns; ++r) h.T_run[r] = -1;
     CU(cudaMemcpyAsync(c->plan.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->plan.slot_T, 0xff, sizeof(int32_t) * c->plan.S, c->stream));   // -1
     CU(hanf::launch_init(c->plan, c->stream));
     int nl = 1;
     CU(hanf::launch_estimate(c->plan, c->stream, &nl));
@@ -327,7 +349,7 @@ int build_graph(hanf_ctx *c)
 int pass_launch_count(const hanf_ctx *c)
 {
     const Plan &p = c->plan;
-    return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + 3;
+    return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) + (p.K > 1 ? 2 : 3);
 }
 
 }  // namespace
@@ -351,6 +373,10 @@ void hanf_default_opts(hanf_opts *o)
     o->gather_variant = 0;
     o->layout = 0;
     o->node_stats = 0;
+    o->num_graphs = 1;
+    o->graph_base = nullptr;
+    o->graph_nodes = nullptr;
+    o->graph_seeds = nullptr;
     o->seeds = nullptr;
     o->stream = nullptr;
 }
@@ -458,6 +484,29 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     int64_t *scan_tmp = reinterpret_cast<int64_t *>(ws + L.scan_tmp);
     int64_t *totals = reinterpret_cast<int64_t *>(ws + L.totals);
 
+    p.K = s.K;
+    p.S = s.S;
+    p.slot_T = reinterpret_cast<int32_t *>(ws + L.slot_T);
+    p.slot_changed = reinterpret_cast<unsigned long long *>(ws + L.slot_changed);
+    if (s.K > 1) {
+        // batch tables: the graph of every 64-node block, bases, node counts
+        std::vector<int32_t> bg(s.nwords, 0);
+        for (int g = 0; g < s.K; ++g)
+            for (int64_t b = o.graph_base[g] >> 6; b < ((o.graph_base[g + 1] + 63) >> 6) && b < s.nwords; ++b)
+                bg[b] = g;
+        int32_t *d_bg = reinterpret_cast<int32_t *>(ws + L.blk_graph);
+        int64_t *d_base = reinterpret_cast<int64_t *>(ws + L.g_base);
+        int64_t *d_nodes = reinterpret_cast<int64_t *>(ws + L.g_nodes);
+        if (cudaMemcpyAsync(d_bg, bg.data(), 4 * s.nwords, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(d_base, o.graph_base, 8 * (s.K + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(d_nodes, o.graph_nodes, 8 * s.K, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return bail(fail(HANF_ECUDA, "batch table upload failed"));
+        p.blk_graph = d_bg;
+        p.g_base = d_base;
+        p.g_nodes = d_nodes;
+    }
+
     // 1. validate the CSR on the device
     if (cudaMemsetAsync(p.ctl, 0, sizeof(DevCtl), st) != cudaSuccess ||
         hanf::launch_validate(p, st) != cudaSuccess || read_ctl(c) != HANF_OK)
@@ -545,12 +594,16 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     }
 
     // 5. run seeds and the linear-counting table m ln(m/V), V = 1..m
-    c->seeds.resize(s.R);
-    for (int r = 0; r < s.R; ++r)
-        c->seeds[r] = o.seeds ? o.seeds[r] : host_splitmix64(seed + (uint64_t)r);
+    c->seeds.resize(s.S);
+    for (int g = 0; g < s.K; ++g)
+        for (int r = 0; r < s.R; ++r) {
+            const uint64_t base_seed = (s.K > 1 && o.graph_seeds) ? o.graph_seeds[g] : seed;
+            c->seeds[(size_t)g * s.R + r] =
+                (s.K == 1 && o.seeds) ? o.seeds[r] : host_splitmix64(base_seed + (uint64_t)r);
+        }
     std::vector<double> lc(s.m + 1, 0.0);
     for (int V = 1; V <= s.m; ++V) lc[V] = (double)s.m * std::log((double)s.m / (double)V);
-    if (cudaMemcpyAsync(const_cast<uint64_t *>(p.seeds), c->seeds.data(), 8 * s.R,
+    if (cudaMemcpyAsync(const_cast<uint64_t *>(p.seeds), c->seeds.data(), 8 * (size_t)s.S,
                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(const_cast<double *>(p.lc), lc.data(), 8 * (s.m + 1),
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -571,8 +624,8 @@ int hanf_estimate(hanf_ctx *c, double *N_out)
     if (!c || !N_out) return fail(HANF_EINVAL, "NULL argument");
     int rc = read_ctl(c);
     if (rc) return rc;
-    CU(cudaMemcpyAsync(N_out, c->plan.hist + (int64_t)c->host_ctl.t * c->plan.R,
-                       sizeof(double) * c->plan.R, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(N_out, c->plan.hist + (int64_t)c->host_ctl.t * c->plan.S,
+                       sizeof(double) * c->plan.S, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return HANF_OK;
 }
@@ -660,17 +713,20 @@ int drive(hanf_ctx *c, double *N_out, int32_t cap, int32_t *T_out, int32_t max_i
         }
     }
     const DevCtl &h = c->host_ctl;
-    const int32_t R = c->plan.R;
+    const int32_t S = c->plan.S;
     const int32_t T = h.t;   // N(0..T) valid (T = t at stop)
     const int32_t have = h.err ? T : T + 1;
-    std::vector<double> hist((size_t)std::max(have, 1) * R);
-    CU(cudaMemcpyAsync(hist.data(), c->plan.hist, sizeof(double) * have * R,
+    std::vector<double> hist((size_t)std::max(have, 1) * S);
+    std::vector<int32_t> slotT(S);
+    CU(cudaMemcpyAsync(hist.data(), c->plan.hist, sizeof(double) * have * S,
                        cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(slotT.data(), c->plan.slot_T, sizeof(int32_t) * S, cudaMemcpyDeviceToHost,
+                       c->stream));
     CU(cudaStreamSynchronize(c->stream));
-    for (int r = 0; r < R; ++r) {
+    for (int r = 0; r < S; ++r) {
         for (int t = 0; t < cap; ++t)
-            N_out[(int64_t)r * cap + t] = t < have ? hist[(size_t)t * R + r] : 0.0;
-        T_out[r] = h.T_run[r] >= 0 ? h.T_run[r] : T;
+            N_out[(int64_t)r * cap + t] = t < have ? hist[(size_t)t * S + r] : 0.0;
+        T_out[r] = slotT[r] >= 0 ? slotT[r] : T;
     }
     if (h.err) return fail(HANF_ERANGE, "no stabilisation within %d passes / %d values", max_iter, cap);
     return HANF_OK;
@@ -786,12 +842,12 @@ namespace {
 struct CkpHeader {
     char magic[8];
     int64_t n, arcs, nwords;
-    int32_t log2m, R, layout, relabel, W, history;
-    uint64_t seeds[hanf::kMaxRuns];
+    int32_t log2m, R, layout, relabel, W, history, K, pad;
+    uint64_t seed_hash;
 };
 
 struct CkpParts {
-    size_t header, ctl, regs, bits, hist, blk, total;
+    size_t header, ctl, regs, bits, hist, blk, slots, total;
 };
 
 CkpParts ckp_parts(const hanf_ctx *c)
@@ -802,9 +858,10 @@ CkpParts ckp_parts(const hanf_ctx *c)
     q.ctl = sizeof(DevCtl);
     q.regs = (size_t)std::max<int64_t>(p.n, 1) * p.W;
     q.bits = (size_t)p.nwords * 8;
-    q.hist = (size_t)p.history_cap * p.R * 8;
+    q.hist = (size_t)p.history_cap * p.S * 8;
     q.blk = (size_t)p.nwords * p.R * 8;
-    q.total = q.header + q.ctl + 2 * q.regs + 2 * q.bits + q.hist + q.blk;
+    q.slots = (size_t)p.S * 4;
+    q.total = q.header + q.ctl + 2 * q.regs + 2 * q.bits + q.hist + q.blk + q.slots;
     return q;
 }
 
@@ -822,7 +879,10 @@ CkpHeader ckp_header(const hanf_ctx *c)
     h.relabel = c->perm != nullptr;
     h.W = c->plan.W;
     h.history = c->plan.history_cap;
-    for (int r = 0; r < c->plan.R; ++r) h.seeds[r] = c->seeds[r];
+    h.K = c->plan.K;
+    uint64_t x = 0x9E3779B97F4A7C15ull;
+    for (uint64_t sd : c->seeds) x = host_splitmix64(x ^ sd);
+    h.seed_hash = x;
     return h;
 }
 
@@ -858,6 +918,7 @@ int hanf_checkpoint_save(hanf_ctx *c, void *buf, size_t bytes)
     d += 2 * q.bits;
     CU(cudaMemcpyAsync(d, p.hist, q.hist, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(d + q.hist, p.blk_part, q.blk, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(d + q.hist + q.blk, p.slot_T, q.slots, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return HANF_OK;
 }
@@ -886,6 +947,7 @@ int hanf_checkpoint_load(hanf_ctx *c, const void *buf, size_t bytes)
     d += 2 * q.bits;
     CU(cudaMemcpyAsync(p.hist, d, q.hist, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(p.blk_part, d + q.hist, q.blk, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.slot_T, d + q.hist + q.blk, q.slots, cudaMemcpyHostToDevice, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     c->host_ctl = ctl;
     return HANF_OK;

@@ -27,9 +27,7 @@ struct DevCtl {
     int32_t err;         // HANF_OK or HANF_ERANGE
     int32_t bad_graph;   // set by the CSR validator
     int32_t pad_;
-    int32_t T_run[kMaxRuns];                 // first pass that left run r unchanged
     unsigned long long changed_count[2];     // nodes changed into regs[parity]
-    unsigned long long run_changed[kMaxRuns];
     unsigned long long last_changed;         // nodes changed by the last pass
     unsigned long long cand_count[2];        // systolic candidates: small, medium degree
     unsigned long long changed_in_arcs;      // in-degree sum of the nodes the last pass changed
@@ -66,10 +64,17 @@ struct Plan {
     uint8_t *hub_any;                 // n_seg flags: segment merged something
     double *blk_part;                 // R x nwords estimator partials
     double *red_part;                 // R x nred
-    double *hist;                     // history_cap x R values of N(t)
+    double *hist;                     // history_cap x S values of N(t)
     const double *lc;                 // m+1 linear-counting values m ln(m/V)
     double amm;                       // alpha_m m^2
-    const uint64_t *seeds;            // R run seeds
+    const uint64_t *seeds;            // S = K * R slot seeds (slot = graph * R + run)
+    // batches of K graphs laid out at 64-aligned node ranges (K = 1: one graph)
+    int32_t K, S;
+    const int32_t *blk_graph;         // graph of every 64-node block (K > 1)
+    const int64_t *g_base;            // K + 1 first stored node of each graph
+    const int64_t *g_nodes;           // K real node counts
+    int32_t *slot_T;                  // S: first pass that left the slot unchanged
+    unsigned long long *slot_changed; // S: nodes changed in the slot this pass
     const int32_t *orig_id;           // input id of every stored node (null: identity)
     // per-node statistics of the E_v(t) sequence, [run][node] (node_stats)
     double *ns_prev;                  // E_v at the last estimate

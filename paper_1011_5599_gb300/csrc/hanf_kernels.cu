@@ -273,9 +273,16 @@ __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, i
     const int lane = threadIdx.x & 31;
     if (lane == 0) atomicAdd(&p.ctl->changed_count[cur ^ 1], (unsigned long long)__popc(bal));
     if (ch) atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
-    for (int r = 0; r < p.R; ++r) {
-        const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u));
-        if (lane == 0 && br) atomicAdd(&p.ctl->run_changed[r], (unsigned long long)__popc(br));
+    if (p.K == 1) {
+        for (int r = 0; r < p.R; ++r) {
+            const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u));
+            if (lane == 0 && br) atomicAdd(&p.slot_changed[r], (unsigned long long)__popc(br));
+        }
+    } else if (ch) {
+        // a batch: lanes may hold nodes of different graphs
+        const int g = __ldg(p.blk_graph + (v >> 6));
+        for (int r = 0; r < p.R; ++r)
+            if ((mask >> r) & 1u) atomicAdd(&p.slot_changed[g * p.R + r], 1ull);
     }
 }
 
@@ -652,7 +659,6 @@ __global__ void k_prep(Plan p)
     c->cand_count[0] = 0;
     c->cand_count[1] = 0;
     c->changed_in_arcs = 0;     // the estimator sums it again after this pass
-    for (int r = 0; r < kMaxRuns; ++r) c->run_changed[r] = 0;
 }
 
 __global__ void k_clear(Plan p)
@@ -661,10 +667,13 @@ __global__ void k_clear(Plan p)
     if (c->done) return;
     unsigned long long *fn = p.F[c->parity ^ 1];
     const bool push = c->mode == kModePush;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.nwords;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.nwords || i < p.S;
          i += (int64_t)gridDim.x * blockDim.x) {
-        fn[i] = 0ull;
-        if (push) p.cand[i] = 0ull;
+        if (i < p.nwords) {
+            fn[i] = 0ull;
+            if (push) p.cand[i] = 0ull;
+        }
+        if (i < p.S) p.slot_changed[i] = 0ull;
     }
 }
 
@@ -722,6 +731,17 @@ __global__ void k_mark(Plan p)
     }
 }
 
+// Slots (graph, run) that a pass left unchanged end at that pass (batches
+// with more than 8 slots; smaller ones are handled by k_post).
+__global__ void k_slot_T(Plan p)
+{
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.S;
+         s += (int64_t)gridDim.x * blockDim.x)
+        if (p.slot_T[s] < 0 && p.slot_changed[s] == 0) p.slot_T[s] = c->t;
+}
+
 // End of a pass: stop if nothing changed (T = t), otherwise advance t and
 // swap the buffers.  In graph mode it also sets the while-node condition.
 __global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
@@ -734,8 +754,9 @@ __global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
         c->last_changed = changed;
         c->passes += 1;
         if (c->mode == kModePush) c->push_passes += 1;
-        for (int r = 0; r < p.R; ++r)
-            if (c->T_run[r] < 0 && c->run_changed[r] == 0) c->T_run[r] = c->t;
+        if (p.S <= 8)
+            for (int r = 0; r < p.S; ++r)
+                if (p.slot_T[r] < 0 && p.slot_changed[r] == 0) p.slot_T[r] = c->t;
         if (changed == 0) {
             c->done = 1;
         } else {
@@ -844,11 +865,16 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
             for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
             if (lane == 0 && d) atomicAdd(&p.ctl->changed_in_arcs, d);
         }
-        const double e0 = v0 < p.n ? node_size(p, rc, v0, r) : 0.0;
-        const double e1 = v1 < p.n ? node_size(p, rc, v1, r) : 0.0;
+        int64_t lim = p.n;   // padding nodes of a batch do not count
+        if (p.K > 1) {
+            const int g = __ldg(p.blk_graph + blk);
+            lim = p.g_base[g] + p.g_nodes[g];
+        }
+        const double e0 = v0 < lim ? node_size(p, rc, v0, r) : 0.0;
+        const double e1 = v1 < lim ? node_size(p, rc, v1, r) : 0.0;
         if (p.node_stats) {
-            if (v0 < p.n) node_stats_update(p, r, v0, e0, all, c->t);
-            if (v1 < p.n) node_stats_update(p, r, v1, e1, all, c->t);
+            if (v0 < lim) node_stats_update(p, r, v0, e0, all, c->t);
+            if (v1 < lim) node_stats_update(p, r, v1, e1, all, c->t);
         }
         double s = e0 + e1;
 #pragma unroll
@@ -879,6 +905,26 @@ __global__ void __launch_bounds__(kBlock) k_est_reduce1(Plan p)
     if (threadIdx.x == 0) p.red_part[(int64_t)r * p.nred + blockIdx.x] = sh[0];
 }
 
+// Batches: N(t) of slot (graph g, run r) = fixed-shape sum of g's block
+// partials, one CTA per slot.
+__global__ void __launch_bounds__(kBlock) k_est_reduce_graphs(Plan p)
+{
+    __shared__ double sh[kBlock];
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    const int slot = blockIdx.x;
+    const int g = slot / p.R, r = slot - g * p.R;
+    const int64_t b0 = p.g_base[g] >> 6, b1 = (p.g_base[g + 1] + 63) >> 6;
+    double s = 0.0;
+    for (int64_t b = b0 + threadIdx.x; b < b1; b += kBlock) s += p.blk_part[(int64_t)r * p.nwords + b];
+    sh[threadIdx.x] = s;
+    for (int w = kBlock / 2; w; w >>= 1) {
+        __syncthreads();
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    }
+    if (threadIdx.x == 0) p.hist[(int64_t)c->t * p.S + slot] = sh[0];
+}
+
 // Second level: N(t) of run r into the history.
 __global__ void __launch_bounds__(kBlock) k_est_reduce2(Plan p)
 {
@@ -893,7 +939,7 @@ __global__ void __launch_bounds__(kBlock) k_est_reduce2(Plan p)
         __syncthreads();
         if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     }
-    if (threadIdx.x == 0) p.hist[(int64_t)c->t * p.R + r] = sh[0];
+    if (threadIdx.x == 0) p.hist[(int64_t)c->t * p.S + r] = sh[0];
 }
 
 // ---------------------------------------------------------------- init
@@ -912,8 +958,14 @@ __global__ void __launch_bounds__(kBlock) k_init(Plan p)
         const int byte0 = (int)(c - v * cpr) << 4;
         const int r = byte0 >> p.b;
         const int o = byte0 & (p.m - 1);
-        const uint64_t item = p.orig_id ? (uint64_t)__ldg(p.orig_id + v) : (uint64_t)v;
-        const uint64_t h = splitmix64(item ^ p.seeds[r]);
+        uint64_t item = p.orig_id ? (uint64_t)__ldg(p.orig_id + v) : (uint64_t)v;
+        int slot = r;
+        if (p.K > 1) {   // a batch: the node's id within its graph, the graph's seeds
+            const int g = __ldg(p.blk_graph + (v >> 6));
+            item = (uint64_t)(v - p.g_base[g]);
+            slot = g * p.R + r;
+        }
+        const uint64_t h = splitmix64(item ^ p.seeds[slot]);
         const int idx = (int)(h >> (64 - p.b));
         const uint64_t rest = h << p.b;
         int rho = rest ? __clzll((long long)rest) + 1 : 64 - p.b + 1;
@@ -943,6 +995,19 @@ __global__ void k_validate(Plan p)
     for (int64_t e = i0; e < p.arcs; e += stride) {
         const int32_t w = p.tgt[e];
         if (w < 0 || (int64_t)w >= p.n) bad = true;
+    }
+    if (p.K > 1 && !bad) {
+        // a batch: arcs stay inside their graph, padding nodes have none
+        for (int64_t v = i0; v < p.n; v += stride) {
+            const int g = p.blk_graph[v >> 6];
+            const int64_t lo = p.g_base[g], hi = lo + p.g_nodes[g];
+            const int64_t b = p.off[v], e = p.off[v + 1];
+            if (v >= hi && e > b) bad = true;
+            for (int64_t k = b; k < e && !bad; ++k) {
+                const int32_t w = p.tgt[k];
+                if (w < lo || w >= hi) bad = true;
+            }
+        }
     }
     if (bad) p.ctl->bad_graph = 1;
 }
@@ -1585,11 +1650,16 @@ __global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
             for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
             if (lane == 0 && d) atomicAdd(&p.ctl->changed_in_arcs, d);
         }
-        const double e0 = v0 < p.n ? pnode_size<P>(p, rc, v0) : 0.0;
-        const double e1 = v1 < p.n ? pnode_size<P>(p, rc, v1) : 0.0;
+        int64_t lim = p.n;
+        if (p.K > 1) {
+            const int g = __ldg(p.blk_graph + blk);
+            lim = p.g_base[g] + p.g_nodes[g];
+        }
+        const double e0 = v0 < lim ? pnode_size<P>(p, rc, v0) : 0.0;
+        const double e1 = v1 < lim ? pnode_size<P>(p, rc, v1) : 0.0;
         if (p.node_stats) {
-            if (v0 < p.n) node_stats_update(p, 0, v0, e0, all, c->t);
-            if (v1 < p.n) node_stats_update(p, 0, v1, e1, all, c->t);
+            if (v0 < lim) node_stats_update(p, 0, v0, e0, all, c->t);
+            if (v1 < lim) node_stats_update(p, 0, v1, e1, all, c->t);
         }
         double s = e0 + e1;
 #pragma unroll
@@ -1604,8 +1674,14 @@ __global__ void __launch_bounds__(kBlock) k_pinit(Plan p)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < p.n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t item = p.orig_id ? (uint64_t)__ldg(p.orig_id + v) : (uint64_t)v;
-        const uint64_t h = splitmix64(item ^ p.seeds[0]);
+        uint64_t item = p.orig_id ? (uint64_t)__ldg(p.orig_id + v) : (uint64_t)v;
+        int slot = 0;
+        if (p.K > 1) {
+            const int g = __ldg(p.blk_graph + (v >> 6));
+            item = (uint64_t)(v - p.g_base[g]);
+            slot = g;
+        }
+        const uint64_t h = splitmix64(item ^ p.seeds[slot]);
         const int idx = (int)(h >> (64 - p.b));
         const uint64_t rest = h << p.b;
         int rho = rest ? __clzll((long long)rest) + 1 : 64 - p.b + 1;
@@ -1801,9 +1877,14 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
     } else {
         k_est_blocks<<<grid_for(p.nwords * p.R, kBlock / 32, 152 * 64), kBlock, 0, s>>>(p);
     }
-    k_est_reduce1<<<dim3((unsigned)p.nred, (unsigned)p.R), kBlock, 0, s>>>(p);
-    k_est_reduce2<<<p.R, kBlock, 0, s>>>(p);
-    if (nlaunch) *nlaunch += 3;
+    if (p.K > 1) {
+        k_est_reduce_graphs<<<p.S, kBlock, 0, s>>>(p);
+        if (nlaunch) *nlaunch += 2;
+    } else {
+        k_est_reduce1<<<dim3((unsigned)p.nred, (unsigned)p.R), kBlock, 0, s>>>(p);
+        k_est_reduce2<<<p.R, kBlock, 0, s>>>(p);
+        if (nlaunch) *nlaunch += 3;
+    }
     return cudaGetLastError();
 }
 
@@ -1811,7 +1892,7 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
                         cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch)
 {
     k_prep<<<1, 1, 0, s>>>(p);
-    k_clear<<<grid_for(p.nwords, kBlock, 152 * 16), kBlock, 0, s>>>(p);
+    k_clear<<<grid_for(std::max<int64_t>(p.nwords, p.S), kBlock, 152 * 16), kBlock, 0, s>>>(p);
     if (p.in_off) k_mark<<<grid_for(p.nwords, kBlock / 32, 152 * 8), kBlock, 0, s>>>(p);
     if (ev0) cudaEventRecord(ev0, s);
     cudaError_t err;
@@ -1836,9 +1917,10 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     }
     if (err != cudaSuccess) return err;
     if (ev1) cudaEventRecord(ev1, s);
+    if (p.S > 8) k_slot_T<<<grid_for(p.S, kBlock, 152 * 4), kBlock, 0, s>>>(p);
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
     if (nlaunch)
-        *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0);
+        *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_estimate(p, s, nlaunch);

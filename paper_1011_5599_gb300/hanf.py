@@ -58,7 +58,10 @@ class Opts(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("dense_den", ctypes.c_int32), ("relabel", ctypes.c_int32),
                 ("gather_variant", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("node_stats", ctypes.c_int32),
+                ("node_stats", ctypes.c_int32), ("num_graphs", ctypes.c_int32),
+                ("graph_base", ctypes.POINTER(ctypes.c_int64)),
+                ("graph_nodes", ctypes.POINTER(ctypes.c_int64)),
+                ("graph_seeds", ctypes.POINTER(ctypes.c_uint64)),
                 ("seeds", ctypes.POINTER(ctypes.c_uint64)), ("stream", ctypes.c_void_p)]
 
 
@@ -161,7 +164,8 @@ def default_opts() -> Opts:
 
 def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=0,
               history_cap=0, use_graph=False, profile=False, seeds=None, stream=None,
-              dense_den=0, relabel=True, gather_variant=0, layout=0, node_stats=False):
+              dense_den=0, relabel=True, gather_variant=0, layout=0, node_stats=False,
+              graph_base=None, graph_nodes=None, graph_seeds=None):
     o = default_opts()
     o.runs = runs
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
@@ -181,6 +185,19 @@ def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=
         keep = (ctypes.c_uint64 * len(seeds))(*[int(s) & (2**64 - 1) for s in seeds])
         o.seeds = ctypes.cast(keep, ctypes.POINTER(ctypes.c_uint64))
     o.stream = stream
+    keep = [keep]
+    if graph_base is not None:
+        K = len(graph_nodes)
+        gb = (ctypes.c_int64 * (K + 1))(*[int(x) for x in graph_base])
+        gn = (ctypes.c_int64 * K)(*[int(x) for x in graph_nodes])
+        o.num_graphs = K
+        o.graph_base = ctypes.cast(gb, ctypes.POINTER(ctypes.c_int64))
+        o.graph_nodes = ctypes.cast(gn, ctypes.POINTER(ctypes.c_int64))
+        keep += [gb, gn]
+        if graph_seeds is not None:
+            gs = (ctypes.c_uint64 * K)(*[int(x) & (2**64 - 1) for x in graph_seeds])
+            o.graph_seeds = ctypes.cast(gs, ctypes.POINTER(ctypes.c_uint64))
+            keep.append(gs)
     return o, keep
 
 
@@ -252,7 +269,8 @@ class HyperANF:
                  hub_min_deg: int = 0, history_cap: int = 0, use_graph: bool = False,
                  profile: bool = False, seeds=None, device=None, stream=None,
                  dense_den: int = 0, relabel: bool = True, gather_variant: int = 0,
-                 layout=0, node_stats: bool = False):
+                 layout=0, node_stats: bool = False, graph_base=None, graph_nodes=None,
+                 graph_seeds=None):
         import torch
 
         self.device = torch.device(device if device is not None else "cuda")
@@ -280,7 +298,12 @@ class HyperANF:
         self._opts, self._seed_keep = make_opts(runs, frontier, push_den, small_max_deg,
                                                 hub_min_deg, history_cap, use_graph, profile,
                                                 seeds, self.stream.cuda_stream, dense_den,
-                                                relabel, gather_variant, layout, node_stats)
+                                                relabel, gather_variant, layout, node_stats,
+                                                graph_base, graph_nodes, graph_seeds)
+        self.K = 1 if graph_nodes is None else len(graph_nodes)
+        self.S = self.K * runs
+        self.graph_base = graph_base
+        self.graph_nodes = graph_nodes
         size = workspace_size(n, arcs, log2m, self._opts, not on_dev)
         self.workspace_bytes = size
         with torch.cuda.device(self.device):
@@ -292,8 +315,32 @@ class HyperANF:
         self._ctx = ctx
 
     # -- Algorithm 2 -------------------------------------------------------
+    @classmethod
+    def batch(cls, graphs, log2m: int, seed: int = 0x5EED, *, graph_seeds=None, **kw):
+        """Many graphs in one context: their padded disjoint union, each graph
+        starting at a multiple of 64 nodes.  N(t) and T come per slot
+        (graph g, run r) = g * runs + r; graph g's registers are the node
+        range [graph_base[g], graph_base[g] + graph_nodes[g])."""
+        degs, tgts, base, nodes = [], [], [0], []
+        for off, tgt in graphs:
+            off = np.asarray(off, dtype=np.int64)
+            n_g = off.size - 1
+            span = -(-n_g // 64) * 64
+            d = np.zeros(span, dtype=np.int64)
+            d[:n_g] = np.diff(off)
+            degs.append(d)
+            tgts.append(np.asarray(tgt, dtype=np.int64) + base[-1])
+            nodes.append(n_g)
+            base.append(base[-1] + span)
+        offsets = np.zeros(base[-1] + 1, dtype=np.int64)
+        if base[-1]:
+            np.cumsum(np.concatenate(degs), out=offsets[1:])
+        targets = (np.concatenate(tgts) if tgts else np.zeros(0)).astype(np.int32)
+        return cls(offsets, targets, log2m, seed, graph_base=base, graph_nodes=nodes,
+                   graph_seeds=graph_seeds, **kw)
+
     def estimate(self) -> np.ndarray:
-        out = np.zeros(self.R, dtype=np.float64)
+        out = np.zeros(self.S, dtype=np.float64)
         check(lib().hanf_estimate(self._ctx, out.ctypes.data_as(ctypes.POINTER(_f64))))
         return out
 
@@ -303,15 +350,16 @@ class HyperANF:
         return ch.value
 
     def run(self, max_iter: int = 4096, cap: int = 4096):
-        """Whole Algorithm 2.  Returns (list of N_r(0..T_r), array of T_r)."""
-        N = np.zeros((self.R, cap), dtype=np.float64)
-        T = np.zeros(self.R, dtype=np.int32)
+        """Whole Algorithm 2.  Returns (list of N_s(0..T_s), array of T_s) for
+        every slot s (= run r for one graph)."""
+        N = np.zeros((self.S, cap), dtype=np.float64)
+        T = np.zeros(self.S, dtype=np.int32)
         check(lib().hanf_run(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)), cap,
                              T.ctypes.data_as(ctypes.POINTER(_i32))))
-        return [N[r, :T[r] + 1].copy() for r in range(self.R)], T
+        return [N[r, :T[r] + 1].copy() for r in range(self.S)], T
 
     def run_raw(self, N: np.ndarray, T: np.ndarray, max_iter: int = 4096) -> int:
-        """hanf_run into caller-provided arrays; returns the status code."""
+        """hanf_run into caller arrays (S x cap, S); returns the status code."""
         return lib().hanf_run(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)),
                               N.shape[1], T.ctypes.data_as(ctypes.POINTER(_i32)))
 
@@ -329,11 +377,11 @@ class HyperANF:
 
     def resume(self, max_iter: int = 4096, cap: int = 4096):
         """Passes from the current state to stabilisation (hanf_continue)."""
-        N = np.zeros((self.R, cap), dtype=np.float64)
-        T = np.zeros(self.R, dtype=np.int32)
+        N = np.zeros((self.S, cap), dtype=np.float64)
+        T = np.zeros(self.S, dtype=np.int32)
         check(lib().hanf_continue(self._ctx, max_iter, N.ctypes.data_as(ctypes.POINTER(_f64)), cap,
                                   T.ctypes.data_as(ctypes.POINTER(_i32))))
-        return [N[r, :T[r] + 1].copy() for r in range(self.R)], T
+        return [N[r, :T[r] + 1].copy() for r in range(self.S)], T
 
     def node_stats(self, run: int = 0, first: int = 0, count: int | None = None) -> dict:
         """reach E_v(T), distance sum and eccentricity estimate per node."""

@@ -332,3 +332,55 @@ def test_node_statistics_match_oracle(H, oracle, kw):
         assert np.array_equal(got[r]["ecc"], ref["ecc"])
         assert np.array_equal(rad[r], ref["radius"])
     assert np.array_equal(sub["dist"], got[0]["dist"][100:150])
+
+
+
+def batch_graphs():
+    return [G.er(500, 2000, seed=1), G.rmat(10, seed=2), G.grid2d(9), G.empty(0), G.path(64),
+            G.clique_path(7, 3), G.er(65, 200, seed=3), G.star(130), G.web(1 << 11, seed=4)]
+
+
+@pytest.mark.parametrize("R,kw", [(1, dict()), (2, dict()), (4, dict(frontier="pull")),
+                                  (1, dict(layout="packed")), (2, dict(use_graph=True)),
+                                  (1, dict(frontier="off", small_max_deg=2, hub_min_deg=8))])
+def test_batch_of_graphs_matches_each_alone(H, oracle, R, kw):
+    """K graphs in one context: every (graph, run) slot has the registers, T
+    and N(t) of that graph run alone with its own seeds."""
+    graphs = batch_graphs()
+    seeds = [100 + 7 * g for g in range(len(graphs))]
+    with H.HyperANF.batch(graphs, 6, graph_seeds=seeds, runs=R, **kw) as h:
+        N, T = h.run()
+        regs = [[h.registers(r, h.graph_base[g], h.graph_nodes[g]) for r in range(R)]
+                for g in range(len(graphs))]
+        assert h.estimate().size == len(graphs) * R
+    for g, (off, tgt) in enumerate(graphs):
+        for r in range(R):
+            No, To, ro = oracle.hyperanf(off, tgt, 6, oracle.run_seed(seeds[g], r), want_regs=True)
+            s = g * R + r
+            assert T[s] == To, (g, r)
+            np.testing.assert_allclose(N[s], No, rtol=RTOL, atol=0)
+            assert np.array_equal(regs[g][r], ro), (g, r)
+
+
+def test_batch_checkpoint_and_rejections(H):
+    graphs = batch_graphs()[:4]
+    with H.HyperANF.batch(graphs, 6, runs=2) as h:
+        N_ref, T_ref = h.run()
+    with H.HyperANF.batch(graphs, 6, runs=2) as h:
+        h.iterate()
+        ckp = h.checkpoint()
+    with H.HyperANF.batch(graphs, 6, runs=2) as h:
+        h.restore(ckp)
+        N, T = h.resume()
+    assert list(T) == list(T_ref) and all(np.array_equal(a, b) for a, b in zip(N, N_ref))
+    # an arc from one graph into another is refused
+    off = np.array([0, 1] + [1] * 63, dtype=np.int64)          # graph 0: node 0 -> 70
+    off = np.concatenate([off, np.full(64, 1, dtype=np.int64)])  # graph 1: no arcs
+    assert off.size == 129
+    tgt = np.array([70], dtype=np.int32)
+    with pytest.raises(H.HanfError) as e:
+        H.HyperANF(off, tgt, 6, graph_base=[0, 64, 128], graph_nodes=[64, 64])
+    assert e.value.code == H.HANF_EINVAL
+    with pytest.raises(H.HanfError) as e:       # bases must be multiples of 64
+        H.HyperANF(*G.empty(100), 6, graph_base=[0, 50, 100], graph_nodes=[50, 50])
+    assert e.value.code == H.HANF_EINVAL
