@@ -336,6 +336,70 @@ def run_serve(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched graphs
+
+def run_batch(args):
+    """Many small graphs: one context (and one graph-captured launch) for the
+    whole batch vs one context per graph, same graphs, identical results."""
+    import numpy as np
+    import torch
+
+    from paper_1011_5599_gb300 import build as B
+    from paper_1011_5599_gb300 import graphs as G
+    B.build()
+    from paper_1011_5599_gb300.hanf import HyperANF
+
+    device = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(device)
+    jobs = G.job_stream(args.jobs, seed=12, rate_per_s=1.0, n_lo=1e3, n_hi=3e4)
+    graphs = [G.job_graph(j) for j in jobs]
+    seeds = [j["seed"] for j in jobs]
+    log2m, R = 6, 4
+    arcs = sum(int(t.size) for _, t in graphs)
+
+    def one_per_graph():
+        out = []
+        for (off, tgt), sd in zip(graphs, seeds):
+            with HyperANF(off, tgt, log2m, sd, runs=R, use_graph=True, device=device) as h:
+                out.append(h.run())
+        return out
+
+    def batched():
+        with HyperANF.batch(graphs, log2m, graph_seeds=[s for s in seeds], runs=R, use_graph=True,
+                            device=device) as h:
+            return h.run()
+
+    for _ in range(2):          # warm-up (allocator, module load)
+        one_per_graph()
+        batched()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single = one_per_graph()
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Nb, Tb = batched()
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    # same T and N(t) to 1e-12 (node order and hence summation order differ:
+    # batches store graphs in input order, single contexts relabel)
+    same = all(single[g][1][r] == Tb[g * R + r]
+               and np.allclose(single[g][0][r], Nb[g * R + r], rtol=1e-12, atol=0)
+               for g in range(len(graphs)) for r in range(R))
+    line = {"metric": "graphs/s (batched in one context vs one context per graph)",
+            "value": len(graphs) / t_batch, "unit": "graphs/s", "n_gpus": 1, "steps": 1,
+            "warmup": 2, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{len(graphs)} graphs, n log-uniform in [1e3, 3e4], mean "
+                                   "degree U[4, 32], ER / R-MAT / grid, m=64, R=4",
+                       "total_arcs": arcs},
+            "one_context_per_graph": {"graphs_s": len(graphs) / t_single, "ms": 1e3 * t_single},
+            "batched": {"graphs_s": len(graphs) / t_batch, "ms": 1e3 * t_batch},
+            "same_T_and_N_within_1e-12": same}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ CUDA arm
 
 def main():
@@ -344,7 +408,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat27", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--workload", default="rmat27",
+                    choices=sorted(WORKLOADS) + ["serve", "batch"])
     ap.add_argument("--jobs", type=int, default=2000, help="served stream: number of jobs")
     ap.add_argument("--pool", type=int, default=100, help="served stream: distinct graphs")
     ap.add_argument("--workers", type=int, default=8, help="served stream: server workers")
@@ -375,6 +440,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "batch":
+        return run_batch(args)
 
     import numpy as np
     import torch
