@@ -349,7 +349,8 @@ int build_graph(hanf_ctx *c)
 int pass_launch_count(const hanf_ctx *c)
 {
     const Plan &p = c->plan;
-    return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) + (p.K > 1 ? 2 : 3);
+    return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
+           (!p.layout && p.W <= 128 ? 1 : 0) + (p.K > 1 ? 2 : 3);
 }
 
 }  // namespace
@@ -585,8 +586,14 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     if (s.transpose) {
         int64_t *in_off = reinterpret_cast<int64_t *>(ws + L.in_off);
         int32_t *in_src = reinterpret_cast<int32_t *>(ws + L.in_src);
+        // after relabelling, regs[1] still holds the input in-degrees and
+        // regs[0] is free scratch for the permuted counts
         if (hanf::launch_transpose(p, in_off, in_src, reinterpret_cast<int64_t *>(p.regs[1]),
-                                   scan_tmp, s.scan_elems, st) != cudaSuccess)
+                                   scan_tmp, s.scan_elems,
+                                   s.relabel ? reinterpret_cast<const unsigned long long *>(p.regs[1])
+                                             : nullptr,
+                                   s.relabel ? p.orig_id : nullptr,
+                                   reinterpret_cast<int64_t *>(p.regs[0]), st) != cudaSuccess)
             return bail(fail(HANF_ECUDA, "transpose failed: %s",
                              cudaGetErrorString(cudaGetLastError())));
         p.in_off = in_off;

@@ -114,7 +114,8 @@ cudaError_t launch_hub_segments(const Plan &p, int32_t d_hub, int64_t *seg_count
                                 int32_t *seg_node, int64_t *seg_beg, int64_t *seg_end,
                                 int32_t *hub_seg_first, int64_t *total_dev, cudaStream_t s);
 cudaError_t launch_transpose(const Plan &p, int64_t *in_off, int32_t *in_src, int64_t *cursor,
-                             int64_t *tmp, int64_t tmp_elems, cudaStream_t s);
+                             int64_t *tmp, int64_t tmp_elems, const unsigned long long *indeg_in,
+                             const int32_t *inv, int64_t *counts, cudaStream_t s);
 int64_t classify_blocks(int64_t n);
 
 // Node relabelling by in-degree class (create time) and the row gather that

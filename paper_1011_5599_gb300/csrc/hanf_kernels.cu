@@ -192,6 +192,59 @@ __device__ __forceinline__ void group_gather(const int32_t *__restrict__ tgt, co
     }
 }
 
+// Sparse variant for passes that test the changed bitmap: most successors
+// fail the test, so a lane group scans UT arcs per batch (UT/LANES targets
+// and bitmap words per lane, all in flight together, the next batch's
+// targets loaded ahead) and gathers the rows that passed in rounds of LANES,
+// skipping empty rounds.
+template <int LANES, int VPL, int UT>
+__device__ __forceinline__ void group_gather_sparse(const int32_t *__restrict__ tgt,
+                                                    const uint8_t *rc,
+                                                    const unsigned long long *Fc, int64_t beg,
+                                                    int64_t end, int gl, unsigned gmask, int gbase,
+                                                    Row<LANES, VPL> &acc, bool &any,
+                                                    uint32_t &gathered)
+{
+    constexpr int TPL = UT / LANES;   // targets per lane and batch
+    int32_t nxt[TPL];
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) {
+        const int64_t j = beg + (int64_t)k * LANES + gl;
+        nxt[k] = j < end ? __ldg(tgt + j) : -1;
+    }
+    for (int64_t e = beg; e < end; e += UT) {
+        int32_t cur[TPL];
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            cur[k] = nxt[k];
+            const int64_t j = e + UT + (int64_t)k * LANES + gl;
+            nxt[k] = j < end ? __ldg(tgt + j) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < TPL; ++k)
+            if (cur[k] >= 0 && !test_bit(Fc, cur[k])) cur[k] = -1;
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            if (!__any_sync(gmask, cur[k] >= 0)) continue;
+            int32_t w[LANES];
+#pragma unroll
+            for (int u = 0; u < LANES; ++u)
+                w[u] = LANES == 1 ? cur[k] : __shfl_sync(gmask, cur[k], gbase + u);
+            Row<LANES, VPL> x[LANES];
+#pragma unroll
+            for (int u = 0; u < LANES; ++u)
+                if (w[u] >= 0) row_load(x[u], rc, w[u], gl);
+#pragma unroll
+            for (int u = 0; u < LANES; ++u)
+                if (w[u] >= 0) {
+                    row_max(acc, x[u]);
+                    any = true;
+                    ++gathered;
+                }
+        }
+    }
+}
+
 // Gather the counters of arcs [beg, end) with the whole warp (beg/end warp-
 // uniform).  Lane i loads target e+i of each batch of 32 (one batch ahead,
 // coalesced) and tests it; lane group g then merges the targets of lanes
@@ -309,13 +362,22 @@ __device__ __forceinline__ void flush_counters(const Plan &p, uint32_t scan, uin
 
 // Union pass over small nodes (degree <= small_max_deg): a lane group per
 // node, GPW nodes per warp, warps striding over the small-node list.
+// Rows of at most 128 bytes get a separate instantiation for passes that test
+// the changed bitmap (SPARSE): each instantiation returns at once when the
+// pass is not its kind, which keeps both register footprints small.
 template <int LANES, int VPL>
+constexpr bool has_sparse_path() { return VPL == 1 && LANES <= 8; }
+
+template <int LANES, int VPL, bool SPARSE>
 __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
 {
     constexpr int GPW = 32 / LANES;
     constexpr int U = 4 / VPL > 0 ? 4 / VPL : 1;
     const DevCtl *ctl = p.ctl;
     if (ctl->done) return;
+    if constexpr (has_sparse_path<LANES, VPL>()) {
+        if (SPARSE != (ctl->mode != kModeDense)) return;
+    }
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
     const bool test = ctl->mode != kModeDense;
@@ -357,8 +419,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
         row_zero(acc);
         bool any = false;
         if (valid) {
-            group_gather<LANES, VPL, U>(p.tgt, rc, Fc, test, beg, end, gl, gmask, gbase, acc, any,
-                                        c_gather);
+            if constexpr (SPARSE)
+                group_gather_sparse<LANES, VPL, 4 * LANES>(p.tgt, rc, Fc, beg, end, gl, gmask,
+                                                           gbase, acc, any, c_gather);
+            else
+                group_gather<LANES, VPL, U>(p.tgt, rc, Fc, test, beg, end, gl, gmask, gbase, acc,
+                                            any, c_gather);
             if (gl == 0) c_scan += (uint32_t)(end - beg);
         }
         const bool inR = valid && !first && test_bit(Fc, v);
@@ -1164,6 +1230,14 @@ __global__ void k_in_degree(Plan p, unsigned long long *cnt)
         atomicAdd(&cnt[p.tgt[e]], 1ull);
 }
 
+__global__ void k_permute_indeg(const unsigned long long *indeg_in, const int32_t *inv, int64_t n,
+                                int64_t *counts)
+{
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u <= n;
+         u += (int64_t)gridDim.x * blockDim.x)
+        counts[u] = u == n ? 0 : (int64_t)indeg_in[inv[u]];
+}
+
 __global__ void k_transpose_fill(Plan p, const int64_t *in_off, unsigned long long *cursor,
                                  int32_t *in_src)
 {
@@ -1440,7 +1514,7 @@ __device__ __forceinline__ uint32_t pnode_finish(const Plan &p, int cur, const P
 template <int P>
 __global__ void __launch_bounds__(kBlock, 3) k_punion_small(Plan p)
 {
-    constexpr int U = P <= 2 ? 4 : (P == 4 ? 2 : 1);
+    constexpr int U = P == 1 ? 4 : (P == 2 ? 2 : 1);
     const DevCtl *ctl = p.ctl;
     if (ctl->done) return;
     const int cur = ctl->parity;
@@ -1500,7 +1574,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_punion_small(Plan p)
 template <int P>
 __global__ void __launch_bounds__(kBlock, 3) k_punion_warp(Plan p)
 {
-    constexpr int U = P <= 2 ? 4 : (P == 4 ? 2 : 1);
+    constexpr int U = P == 1 ? 4 : (P == 2 ? 2 : 1);
     const DevCtl *ctl = p.ctl;
     if (ctl->done) return;
     const int cur = ctl->parity;
@@ -1757,7 +1831,9 @@ struct UnionKernels {
         } else {
             k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
         }
-        k_union_small<LANES, VPL><<<sblocks, kBlock, 0, s>>>(p);
+        k_union_small<LANES, VPL, false><<<sblocks, kBlock, 0, s>>>(p);
+        if constexpr (has_sparse_path<LANES, VPL>())
+            k_union_small<LANES, VPL, true><<<sblocks, kBlock, 0, s>>>(p);
         return cudaGetLastError();
     }
     static cudaError_t launch_hub(const Plan &p, cudaStream_t s)
@@ -1770,7 +1846,7 @@ struct UnionKernels {
     static int occupancy()
     {
         int a = 0, b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_union_small<LANES, VPL>, kBlock, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_union_small<LANES, VPL, false>, kBlock, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_union_warp<LANES, VPL>, kBlock, 0);
         return a < b ? a : b;
     }
@@ -1920,7 +1996,8 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     if (p.S > 8) k_slot_T<<<grid_for(p.S, kBlock, 152 * 4), kBlock, 0, s>>>(p);
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
     if (nlaunch)
-        *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0);
+        *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
+                    (!p.layout && p.W <= 128 ? 1 : 0);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_estimate(p, s, nlaunch);
@@ -1995,12 +2072,21 @@ cudaError_t launch_hub_segments(const Plan &p, int32_t d_hub, int64_t *seg_count
 }
 
 cudaError_t launch_transpose(const Plan &p, int64_t *in_off, int32_t *in_src, int64_t *cursor,
-                             int64_t *tmp, int64_t tmp_elems, cudaStream_t s)
+                             int64_t *tmp, int64_t tmp_elems, const unsigned long long *indeg_in,
+                             const int32_t *inv, int64_t *counts, cudaStream_t s)
 {
-    cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (p.n + 1), s);
-    k_in_degree<<<grid_for(p.arcs, kBlock, 152 * 64), kBlock, 0, s>>>(
-        p, reinterpret_cast<unsigned long long *>(cursor));
-    cudaError_t err = scan_exclusive_i64(cursor, in_off, p.n + 1, tmp, tmp_elems, s);
+    cudaError_t err;
+    if (indeg_in && inv) {
+        // relabelled graph: in-degrees are the input ones, permuted
+        k_permute_indeg<<<grid_for(p.n + 1, kBlock, 152 * 64), kBlock, 0, s>>>(indeg_in, inv, p.n,
+                                                                              counts);
+        err = scan_exclusive_i64(counts, in_off, p.n + 1, tmp, tmp_elems, s);
+    } else {
+        cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (p.n + 1), s);
+        k_in_degree<<<grid_for(p.arcs, kBlock, 152 * 64), kBlock, 0, s>>>(
+            p, reinterpret_cast<unsigned long long *>(cursor));
+        err = scan_exclusive_i64(cursor, in_off, p.n + 1, tmp, tmp_elems, s);
+    }
     if (err != cudaSuccess) return err;
     cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (p.n + 1), s);
     k_transpose_fill<<<152 * 16, kBlock, 0, s>>>(p, in_off,
