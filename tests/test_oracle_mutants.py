@@ -22,7 +22,8 @@ MUTANTS = {
     "no_rho_clamp": ("if (r > 31) r = 31;", ""),
     "no_linear_counting": ("if (E <= 2.5 * (double)m && V > 0)", "if (0)"),
     "alpha64_wrong": ("if (m == 64) return 0.709;", "if (m == 64) return 0.7213;"),
-    "sum_skips_node0": ("for (v = 0; v < n; ++v) {\n        double x", "for (v = 1; v < n; ++v) {\n        double x"),
+    "sum_skips_node0": ("for (v = 0; v < n; ++v) {\n        double x = ora_size(",
+                        "for (v = 1; v < n; ++v) {\n        double x = ora_size("),
     "stop_one_pass_late": ("if (changed == 0) break;", "if (changed == 0) { if (t < cap - 1) { ++t; N_out[t] = N_out[t - 1]; } break; }"),
     "stop_one_pass_early": ("if (changed == 0) break;\n        ++t;", "++t;\n        if (changed <= 1) break;"),
     "variance_sign": ("out[3] = sq - mean * mean;", "out[3] = sq + mean * mean;"),
