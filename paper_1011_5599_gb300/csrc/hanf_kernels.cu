@@ -38,6 +38,14 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 
 // ---------------------------------------------------------------- rows
 
+// Resident blocks per SM the union kernels are compiled for: three (at most
+// 80 registers a thread) while a lane holds one 16-byte vector of a row,
+// two where it holds several, so that the rows in flight stay in registers.
+__host__ __device__ constexpr int min_blocks(int vectors_per_lane)
+{
+    return vectors_per_lane >= 2 ? 2 : 3;
+}
+
 template <int LANES, int VPL>
 struct Row {
     uint4 v[VPL];
@@ -195,8 +203,8 @@ __device__ __forceinline__ void group_gather(const int32_t *__restrict__ tgt, co
 // Sparse variant for passes that test the changed bitmap: most successors
 // fail the test, so a lane group scans UT arcs per batch (UT/LANES targets
 // and bitmap words per lane, all in flight together, the next batch's
-// targets loaded ahead) and gathers the rows that passed in rounds of LANES,
-// skipping empty rounds.
+// targets loaded ahead), then gathers only the rows that passed, packed into
+// rounds of at most SUBR rows.
 template <int LANES, int VPL, int UT>
 __device__ __forceinline__ void group_gather_sparse(const int32_t *__restrict__ tgt,
                                                     const uint8_t *rc,
@@ -206,6 +214,7 @@ __device__ __forceinline__ void group_gather_sparse(const int32_t *__restrict__ 
                                                     uint32_t &gathered)
 {
     constexpr int TPL = UT / LANES;   // targets per lane and batch
+    constexpr int SUBR = LANES < 4 ? LANES : 4;
     int32_t nxt[TPL];
 #pragma unroll
     for (int k = 0; k < TPL; ++k) {
@@ -225,22 +234,30 @@ __device__ __forceinline__ void group_gather_sparse(const int32_t *__restrict__ 
             if (cur[k] >= 0 && !test_bit(Fc, cur[k])) cur[k] = -1;
 #pragma unroll
         for (int k = 0; k < TPL; ++k) {
-            if (!__any_sync(gmask, cur[k] >= 0)) continue;
-            int32_t w[LANES];
+            // lanes of this group holding a target that passed (absolute
+            // lane bits; the same value on every lane of the group)
+            unsigned live = __ballot_sync(gmask, cur[k] >= 0) & gmask;
+            while (live) {
+                int32_t w[SUBR];
 #pragma unroll
-            for (int u = 0; u < LANES; ++u)
-                w[u] = LANES == 1 ? cur[k] : __shfl_sync(gmask, cur[k], gbase + u);
-            Row<LANES, VPL> x[LANES];
-#pragma unroll
-            for (int u = 0; u < LANES; ++u)
-                if (w[u] >= 0) row_load(x[u], rc, w[u], gl);
-#pragma unroll
-            for (int u = 0; u < LANES; ++u)
-                if (w[u] >= 0) {
-                    row_max(acc, x[u]);
-                    any = true;
-                    ++gathered;
+                for (int u = 0; u < SUBR; ++u) {
+                    const int src = live ? __ffs(live) - 1 : gbase;
+                    w[u] = __shfl_sync(gmask, cur[k], src);
+                    if (!live) w[u] = -1;
+                    live &= live - 1u;
                 }
+                Row<LANES, VPL> x[SUBR];
+#pragma unroll
+                for (int u = 0; u < SUBR; ++u)
+                    if (w[u] >= 0) row_load(x[u], rc, w[u], gl);
+#pragma unroll
+                for (int u = 0; u < SUBR; ++u)
+                    if (w[u] >= 0) {
+                        row_max(acc, x[u]);
+                        any = true;
+                        ++gathered;
+                    }
+            }
         }
     }
 }
@@ -314,28 +331,50 @@ __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Ro
     return mask;
 }
 
-// Record the nodes whose counters changed: bitmap bit, node count and
-// per-run counts, all with fire-and-forget reductions so that no warp waits
-// on them.  Called by all lanes; `leader` marks one lane per node.
+// Changed-node tallies of one thread, kept in registers for the whole kernel
+// and flushed once at its end: a reduction per node on the few shared
+// counters would queue every warp of the GPU on one L2 slice.
+struct MarkTally {
+    uint32_t nodes = 0;   // lane 0: changed nodes seen by the warp
+    uint32_t runs = 0;    // lane r < R: nodes whose run-r counter changed (one graph)
+};
+
+// Record the nodes whose counters changed: the bitmap bit at once (a
+// fire-and-forget reduction), the counts in the tally.  Called by all lanes;
+// `leader` marks one lane per node, `mask` is its mask of changed runs.
 __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, int32_t v,
-                                          uint32_t mask)
+                                          uint32_t mask, MarkTally &mt)
 {
     const bool ch = leader && mask != 0;
     const unsigned bal = __ballot_sync(kFull, ch);
     if (bal == 0) return;
     const int lane = threadIdx.x & 31;
-    if (lane == 0) atomicAdd(&p.ctl->changed_count[cur ^ 1], (unsigned long long)__popc(bal));
+    if (lane == 0) mt.nodes += __popc(bal);
     if (ch) atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
     if (p.K == 1) {
-        for (int r = 0; r < p.R; ++r) {
-            const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u));
-            if (lane == 0 && br) atomicAdd(&p.slot_changed[r], (unsigned long long)__popc(br));
+        // lane r counts run r: read the changed leaders' masks, or ballot
+        // run by run, whichever takes fewer warp operations
+        if (__popc(bal) < p.R) {
+            for (unsigned b = bal; b; b &= b - 1u) {
+                const uint32_t mg = __shfl_sync(kFull, mask, __ffs(b) - 1);
+                mt.runs += (mg >> lane) & 1u;
+            }
+        } else {
+            for (int r = 0; r < p.R; ++r) {
+                const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u));
+                if (lane == r) mt.runs += __popc(br);
+            }
         }
-    } else if (ch) {
-        // a batch: lanes may hold nodes of different graphs
-        const int g = __ldg(p.blk_graph + (v >> 6));
-        for (int r = 0; r < p.R; ++r)
-            if ((mask >> r) & 1u) atomicAdd(&p.slot_changed[g * p.R + r], 1ull);
+    } else {
+        // a batch: lanes may hold nodes of different graphs; one reduction
+        // per graph present and run
+        const int g = ch ? __ldg(p.blk_graph + (v >> 6)) : -1;
+        const unsigned peers = __match_any_sync(kFull, g);
+        const bool head = ch && __ffs(peers) - 1 == lane;
+        for (int r = 0; r < p.R; ++r) {
+            const unsigned br = __ballot_sync(kFull, ch && ((mask >> r) & 1u)) & peers;
+            if (head && br) atomicAdd(&p.slot_changed[g * p.R + r], (unsigned long long)__popc(br));
+        }
     }
 }
 
@@ -346,18 +385,23 @@ __device__ __forceinline__ unsigned warp_sum_u32(unsigned x)
     return x;
 }
 
-__device__ __forceinline__ void flush_counters(const Plan &p, uint32_t scan, uint32_t gather,
-                                               uint32_t own, uint32_t write)
+__device__ __forceinline__ void flush_counters(const Plan &p, int cur, const MarkTally &mt,
+                                               uint32_t scan, uint32_t gather, uint32_t own,
+                                               uint32_t write)
 {
     const unsigned s0 = warp_sum_u32(scan), s1 = warp_sum_u32(gather);
     const unsigned s2 = warp_sum_u32(own), s3 = warp_sum_u32(write);
-    if ((threadIdx.x & 31) == 0) {
-        DevCtl *c = p.ctl;
+    const int lane = threadIdx.x & 31;
+    DevCtl *c = p.ctl;
+    if (lane == 0) {
         if (s0) atomicAdd(&c->arcs_scanned, (unsigned long long)s0);
         if (s1) atomicAdd(&c->arcs_gathered, (unsigned long long)s1);
         if (s2) atomicAdd(&c->own_reads, (unsigned long long)s2);
         if (s3) atomicAdd(&c->writes, (unsigned long long)s3);
+        if (mt.nodes) atomicAdd(&c->changed_count[cur ^ 1], (unsigned long long)mt.nodes);
     }
+    if (p.K == 1 && lane < p.R && mt.runs)
+        atomicAdd(&p.slot_changed[lane], (unsigned long long)mt.runs);
 }
 
 // Union pass over small nodes (degree <= small_max_deg): a lane group per
@@ -369,7 +413,7 @@ template <int LANES, int VPL>
 constexpr bool has_sparse_path() { return VPL == 1 && LANES <= 8; }
 
 template <int LANES, int VPL, bool SPARSE>
-__global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
+__global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
 {
     constexpr int GPW = 32 / LANES;
     constexpr int U = 4 / VPL > 0 ? 4 / VPL : 1;
@@ -390,6 +434,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
     // systolic passes visit the small-degree candidates only
     const int32_t *list = push ? p.cand_list[0] : p.nodes;
     const int64_t count = push ? (int64_t)ctl->cand_count[0] : p.n_small;
@@ -431,9 +476,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
         const bool need = valid && (any || inR);
         const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write,
                                           own_early ? &own : nullptr);
-        warp_mark(p, cur, gl == 0 && valid, v, mask);
+        warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
-    flush_counters(p, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
+    flush_counters(p, cur, mt, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
 }
 
 // Union pass over medium nodes (a warp per node) and hub segments (a warp
@@ -441,7 +486,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small(Plan p)
 // by k_hub_finish).  Hub segments come first so the longest items start
 // early.
 template <int LANES, int VPL>
-__global__ void __launch_bounds__(kBlock, 3) k_union_warp(Plan p)
+__global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
 {
     const DevCtl *ctl = p.ctl;
     if (ctl->done) return;
@@ -458,6 +503,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_warp(Plan p)
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
     for (int64_t it = warp; it < total; it += nwarps) {
         const bool seg = it < p.n_seg;
         const int32_t v = seg ? __ldg(p.seg_node + it) : __ldg(med + (it - p.n_seg));
@@ -480,10 +526,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_warp(Plan p)
             const bool inR = take && !first && test_bit(Fc, v);
             const bool need = take && (any || inR) && g == 0;
             const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
-            warp_mark(p, cur, lane == 0, v, mask);
+            warp_mark(p, cur, lane == 0, v, mask, mt);
         }
     }
-    flush_counters(p, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
+    flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
 }
 
 // ---------------------------------------------------------------- asynchronous gathers
@@ -551,6 +597,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
 
     // ---- producer state (warp-uniform) ----
     int64_t p_it = warp - nwarps, p_e = 0, p_end = 0;
@@ -641,7 +688,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
                 const bool inR = !first && test_bit(Fc, v);
                 const bool need = (anyw || inR) && g == 0;
                 const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
-                warp_mark(p, cur, lane == 0, v, mask);
+                warp_mark(p, cur, lane == 0, v, mask, mt);
             }
             row_zero(acc);
             any = false;
@@ -656,7 +703,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
         if (!consume(k % D) && p_it >= total) break;
     }
     cp_async_wait<0>();
-    flush_counters(p, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
+    flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
 }
 
 // Hub nodes: combine the segment partials written by k_union_warp, then
@@ -675,6 +722,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_own = 0, c_write = 0;
+    MarkTally mt;
     for (int64_t base = warp * GPW; base < p.n_hub; base += nwarps * GPW) {
         const int64_t h = base + g;
         const bool valid = h < p.n_hub;
@@ -696,9 +744,9 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
         const bool inR = take && !first && test_bit(Fc, v);
         const bool need = take && (any || inR);
         const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
-        warp_mark(p, cur, gl == 0 && valid, v, mask);
+        warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
-    flush_counters(p, 0u, 0u, c_own, c_write);
+    flush_counters(p, cur, mt, 0u, 0u, c_own, c_write);
 }
 
 // ---------------------------------------------------------------- pass control
@@ -914,6 +962,7 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long cia = 0;   // in-arcs of changed nodes, flushed once
     const int64_t items = p.nwords * p.R;
     for (int64_t it = warp; it < items; it += nwarps) {
         const int r = (int)(it / p.nwords);
@@ -929,7 +978,7 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
             if ((word >> (lane + 32)) & 1ull) d += (unsigned long long)(p.in_off[v1 + 1] - p.in_off[v1]);
 #pragma unroll
             for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-            if (lane == 0 && d) atomicAdd(&p.ctl->changed_in_arcs, d);
+            cia += d;   // warp-uniform after the butterfly
         }
         int64_t lim = p.n;   // padding nodes of a batch do not count
         if (p.K > 1) {
@@ -947,6 +996,7 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0) p.blk_part[it] = s;
     }
+    if (lane == 0 && cia) atomicAdd(&p.ctl->changed_in_arcs, cia);
 }
 
 // Fixed-shape tree over the block partials: first level, one CTA per run and
@@ -1512,7 +1562,7 @@ __device__ __forceinline__ uint32_t pnode_finish(const Plan &p, int cur, const P
 
 // Small nodes: a lane per node, U arcs in flight per lane.
 template <int P>
-__global__ void __launch_bounds__(kBlock, 3) k_punion_small(Plan p)
+__global__ void __launch_bounds__(kBlock, P >= 8 ? 1 : min_blocks(P / 2)) k_punion_small(Plan p)
 {
     constexpr int U = P == 1 ? 4 : (P == 2 ? 2 : 1);
     const DevCtl *ctl = p.ctl;
@@ -1530,6 +1580,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_punion_small(Plan p)
     const int32_t *list = push ? p.cand_list[0] : p.nodes;
     const int64_t count = push ? (int64_t)ctl->cand_count[0] : p.n_small;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
     for (int64_t base = warp * 32; base < count; base += nwarps * 32) {
         const int64_t idx = base + lane;
         const bool valid = idx < count;
@@ -1564,15 +1615,15 @@ __global__ void __launch_bounds__(kBlock, 3) k_punion_small(Plan p)
         const bool inR = valid && !first && test_bit(Fc, v);
         const uint32_t mask = pnode_finish(p, cur, acc, valid && (any || inR), inR, v, c_own,
                                            c_write, own_early ? &own : nullptr);
-        warp_mark(p, cur, valid, v, mask);
+        warp_mark(p, cur, valid, v, mask, mt);
     }
-    flush_counters(p, c_scan, c_gather, c_own, c_write);
+    flush_counters(p, cur, mt, c_scan, c_gather, c_own, c_write);
 }
 
 // Medium nodes and hub segments: a warp per item, lane i merges arcs
 // e+i, e+i+32, ... (U per lane in flight), then a warp-wide max.
 template <int P>
-__global__ void __launch_bounds__(kBlock, 3) k_punion_warp(Plan p)
+__global__ void __launch_bounds__(kBlock, P >= 8 ? 1 : min_blocks(P / 2)) k_punion_warp(Plan p)
 {
     constexpr int U = P == 1 ? 4 : (P == 2 ? 2 : 1);
     const DevCtl *ctl = p.ctl;
@@ -1589,6 +1640,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_punion_warp(Plan p)
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
     for (int64_t it = warp; it < total; it += nwarps) {
         const bool seg = it < p.n_seg;
         const int32_t v = seg ? __ldg(p.seg_node + it) : __ldg(med + (it - p.n_seg));
@@ -1631,10 +1683,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_punion_warp(Plan p)
             const bool inR = take && !first && test_bit(Fc, v);
             const bool need = take && (any || inR) && lane == 0;
             const uint32_t mask = pnode_finish(p, cur, acc, need, inR, v, c_own, c_write);
-            warp_mark(p, cur, lane == 0, v, mask);
+            warp_mark(p, cur, lane == 0, v, mask, mt);
         }
     }
-    flush_counters(p, c_scan, c_gather, c_own, c_write);
+    flush_counters(p, cur, mt, c_scan, c_gather, c_own, c_write);
 }
 
 // Hub nodes: combine the segment partials, a lane per hub.
@@ -1650,6 +1702,7 @@ __global__ void __launch_bounds__(kBlock) k_phub_finish(Plan p)
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     uint32_t c_own = 0, c_write = 0;
+    MarkTally mt;
     for (int64_t base = tid - (threadIdx.x & 31); base < p.n_hub; base += nthreads) {
         const int64_t h = base + (threadIdx.x & 31);
         const bool valid = h < p.n_hub;
@@ -1670,9 +1723,9 @@ __global__ void __launch_bounds__(kBlock) k_phub_finish(Plan p)
         }
         const bool inR = take && !first && test_bit(Fc, v);
         const uint32_t mask = pnode_finish(p, cur, acc, take && (any || inR), inR, v, c_own, c_write);
-        warp_mark(p, cur, valid, v, mask);
+        warp_mark(p, cur, valid, v, mask, mt);
     }
-    flush_counters(p, 0u, 0u, c_own, c_write);
+    flush_counters(p, cur, mt, 0u, 0u, c_own, c_write);
 }
 
 // size() of a packed counter: V = empty registers; sum_j 2^(31-M[j]) taken
@@ -1712,6 +1765,7 @@ __global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long cia = 0;   // in-arcs of changed nodes, flushed once
     for (int64_t blk = warp; blk < p.nwords; blk += nwarps) {
         if (!all && Fc[blk] == 0ull) continue;
         const int64_t v0 = blk * 64 + lane, v1 = v0 + 32;
@@ -1722,7 +1776,7 @@ __global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
             if ((word >> (lane + 32)) & 1ull) d += (unsigned long long)(p.in_off[v1 + 1] - p.in_off[v1]);
 #pragma unroll
             for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-            if (lane == 0 && d) atomicAdd(&p.ctl->changed_in_arcs, d);
+            cia += d;   // warp-uniform after the butterfly
         }
         int64_t lim = p.n;
         if (p.K > 1) {
@@ -1740,6 +1794,7 @@ __global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0) p.blk_part[blk] = s;
     }
+    if (lane == 0 && cia) atomicAdd(&p.ctl->changed_in_arcs, cia);
 }
 
 // Algorithm 2's initialisation in the packed layout: node v adds itself.
