@@ -422,6 +422,9 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
     ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--scatter-den", type=int, default=0,
+                    help="pure-push passes below arcs/scatter_den changed in-arcs (0 = library "
+                         "default, negative = never)")
     ap.add_argument("--layout", default="byte", choices=["byte", "packed"],
                     help="register layout: one byte each, or five bit-planes")
     ap.add_argument("--autotune", action="store_true",
@@ -487,7 +490,8 @@ def main():
         print(json.dumps({"autotune": tuned, "best_ms": tune_ms,
                           "tuning_s": time.perf_counter() - t_tune}), file=sys.stderr)
     h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
-                 use_graph=args.driver == "graph", profile=args.driver == "host", **tuned)
+                 use_graph=args.driver == "graph", profile=args.driver == "host",
+                 scatter_den=args.scatter_den, **tuned)
     for _ in range(args.warmup):
         h.run()
 
@@ -587,6 +591,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": wl["text"], "n": n, "arcs": arcs, "m": m, "runs": R,
                        "layout": args.layout, "frontier": "auto", "driver": args.driver,
+                       "scatter_den": args.scatter_den or "default",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (no flush)", "tuned": tuned,
                        "graph_gen_s": round(t_gen, 2)},

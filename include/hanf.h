@@ -61,7 +61,10 @@ extern "C" {
 #define HANF_FRONTIER_OFF 0  /* every pass merges every arc                  */
 #define HANF_FRONTIER_PULL 1 /* skip successors that did not change          */
 #define HANF_FRONTIER_AUTO 2 /* PULL, and systolic push through the transpose
-                                when fewer than n/push_den counters changed   */
+                                when fewer than n/push_den counters changed,
+                                or a pure push (scatter) when the changed
+                                counters have fewer than arcs/scatter_den
+                                in-arcs                                       */
 
 typedef struct hanf_ctx hanf_ctx;
 
@@ -104,6 +107,11 @@ typedef struct hanf_opts {
                               splitmix64(graph_seeds[g] + r); NULL = seed      */
     const uint64_t *seeds; /* R explicit run seeds (host, K = 1), or NULL     */
     void *stream;          /* cudaStream_t for every launch; NULL = default    */
+    int32_t scatter_den;   /* frontier AUTO: pure push (scatter) pass while the
+                              nodes changed by the last pass have fewer than
+                              arcs/scatter_den in-arcs (byte layout); 0 = 8
+                              for rows of at most 128 bytes (R*m), never for
+                              wider rows; negative = never                   */
 } hanf_opts;
 
 /* Fill *opts with the defaults above. */

@@ -346,11 +346,23 @@ int build_graph(hanf_ctx *c)
     return HANF_OK;
 }
 
+// Status of a loop stopped by the device: ERANGE (history or pass limit) or
+// ESTATE (a scatter pass found a register outside 0..31).
+int ctl_fail(int32_t err)
+{
+    if (err == HANF_ESTATE)
+        return fail(HANF_ESTATE, "a scatter pass exceeded its compare-and-swap bound "
+                                 "(registers outside 0..31)");
+    return fail(err, "history capacity exhausted");
+}
+
 int pass_launch_count(const hanf_ctx *c)
 {
     const Plan &p = c->plan;
     return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
-           (!p.layout && p.W <= 128 ? 1 : 0) + (p.K > 1 ? 2 : 3);
+           (!p.layout && p.W <= 128 ? 1 : 0) +
+           (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0) +
+           (p.K > 1 ? 2 : 3);
 }
 
 }  // namespace
@@ -370,6 +382,7 @@ void hanf_default_opts(hanf_opts *o)
     o->use_graph = 0;
     o->profile = 0;
     o->dense_den = 0;
+    o->scatter_den = 0;
     o->relabel = 1;
     o->gather_variant = 0;
     o->layout = 0;
@@ -443,6 +456,13 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.frontier = o.frontier;
     p.push_den = o.push_den;
     p.dense_den = o.dense_den ? o.dense_den : 2;
+    // scatter passes by default for rows of at most 128 bytes: with wider rows a
+    // pushed pair costs a whole row of compare-and-swaps and the systolic pull
+    // measured faster (web-like graph, 512-byte rows)
+    p.scatter_den = o.scatter_den == 0 ? (p.W <= 128 && !p.layout ? 8 : 0)
+                                       : std::max(o.scatter_den, 0);
+    p.scatter_seg = 2048;     // in-arcs per segment of a long in-list
+    p.scatter_inline = 256;   // in-lists up to this length are pushed whole
     p.history_cap = s.history;
     cudaStream_t st = c->stream;
     if (s.copy_graph) {
@@ -617,6 +637,7 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
         return bail(fail(HANF_ECUDA, "constant upload failed"));
     p.union_warps = s.layout ? hanf::packed_occupancy_warps(s.m, c->nsm)
                              : hanf::union_occupancy_warps(s.W, c->nsm);
+    p.scatter_warps = s.layout ? 0 : hanf::scatter_occupancy_warps(s.W, c->nsm);
     p.union_async_warps = s.layout ? 0 : hanf::union_async_warps(s.W, c->nsm);
     p.warp_variant = (o.gather_variant == 2 && p.union_async_warps > 0) ? 2 : 1;
 
@@ -644,12 +665,12 @@ int hanf_iterate(hanf_ctx *c, int64_t *changed_out)
     if (rc) return rc;
     if (c->host_ctl.done) {
         if (changed_out) *changed_out = 0;
-        return c->host_ctl.err ? fail(c->host_ctl.err, "history capacity exhausted") : HANF_OK;
+        return c->host_ctl.err ? ctl_fail(c->host_ctl.err) : HANF_OK;
     }
     rc = one_pass(c);
     if (rc) return rc;
     if (changed_out) *changed_out = (int64_t)c->host_ctl.last_changed;
-    if (c->host_ctl.err) return fail(c->host_ctl.err, "history capacity exhausted");
+    if (c->host_ctl.err) return ctl_fail(c->host_ctl.err);
     return HANF_OK;
 }
 
@@ -735,6 +756,7 @@ int drive(hanf_ctx *c, double *N_out, int32_t cap, int32_t *T_out, int32_t max_i
             N_out[(int64_t)r * cap + t] = t < have ? hist[(size_t)t * S + r] : 0.0;
         T_out[r] = slotT[r] >= 0 ? slotT[r] : T;
     }
+    if (h.err == HANF_ESTATE) return ctl_fail(h.err);
     if (h.err) return fail(HANF_ERANGE, "no stabilisation within %d passes / %d values", max_iter, cap);
     return HANF_OK;
 }

@@ -22,9 +22,10 @@ struct DevCtl {
     int32_t t;           // passes completed since initialisation
     int32_t parity;      // regs[parity] holds c_t, F[parity] the nodes changed into it
     int32_t done;        // 1 once a pass changed no counter
-    int32_t mode;        // coming pass: 0 pull + bitmap test, 1 systolic push, 2 dense pull
+    int32_t mode;        // coming pass: 0 pull + bitmap test, 1 systolic push, 2 dense pull,
+                         // 3 scatter (pure push)
     int32_t max_t;       // stop (with err = HANF_ERANGE) after this many passes
-    int32_t err;         // HANF_OK or HANF_ERANGE
+    int32_t err;         // HANF_OK, HANF_ERANGE, or HANF_ESTATE (a scatter bound broken)
     int32_t bad_graph;   // set by the CSR validator
     int32_t pad_;
     unsigned long long changed_count[2];     // nodes changed into regs[parity]
@@ -84,9 +85,12 @@ struct Plan {
     int32_t *ns_rad;                  // first t with E_v(t) >= ns_alpha E_v(T)
     double ns_alpha;
     int32_t node_stats, ns_radius_mode;
-    int32_t frontier, push_den, dense_den;
+    int32_t frontier, push_den, dense_den, scatter_den;
+    int32_t scatter_seg;              // scatter passes: in-arcs per segment, and the
+    int32_t scatter_inline;           // in-degree above which a list is segmented
     int32_t history_cap;
     int32_t union_warps;              // resident warps of the union launch
+    int32_t scatter_warps;            // resident warps of the scatter launch
     int32_t union_async_warps;        // resident warps of the asynchronous-copy variant
     int32_t warp_variant;             // medium/hub gathers: 1 register batches, 2 async copies
     DevCtl *ctl;
@@ -99,6 +103,7 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch);
 cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
                         cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch);
 int union_occupancy_warps(int W, int nsm);
+int scatter_occupancy_warps(int W, int nsm);
 int packed_occupancy_warps(int m, int nsm);
 int union_async_warps(int W, int nsm);
 

@@ -149,9 +149,13 @@ __device__ __forceinline__ bool test_bit(const unsigned long long *bits, int32_t
 //   kModeDense  pull without the per-arc test, used at t = 0, with the
 //               frontier off, and while most counters still change: merging an
 //               unchanged successor is harmless, max being idempotent.
+//   kModeScatter pure push: each node changed by the last pass raises the new
+//               counters of its predecessors (k_scatter), used once the changed
+//               nodes have few in-arcs; the pull kernels sit the pass out.
 constexpr int kModeTest = 0;
 constexpr int kModePush = 1;
 constexpr int kModeDense = 2;
+constexpr int kModeScatter = 3;
 
 // Gather the counters of arcs [beg, end) of one node, one lane group per
 // node (all lanes of the group share beg/end).  Each lane loads U/LANES
@@ -336,21 +340,17 @@ __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Ro
 // counters would queue every warp of the GPU on one L2 slice.
 struct MarkTally {
     uint32_t nodes = 0;   // lane 0: changed nodes seen by the warp
-    uint32_t runs = 0;    // lane r < R: nodes whose run-r counter changed (one graph)
+    uint32_t fresh = 0;   // any lane: nodes it marked first (scatter passes)
+    uint32_t runs = 0;    // lane r < R: nodes whose run-r counter changed (one graph;
+                          // in scatter passes raises, which may repeat a node)
 };
 
-// Record the nodes whose counters changed: the bitmap bit at once (a
-// fire-and-forget reduction), the counts in the tally.  Called by all lanes;
-// `leader` marks one lane per node, `mask` is its mask of changed runs.
-__device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, int32_t v,
-                                          uint32_t mask, MarkTally &mt)
+// Per-run change tallies of the nodes marked by one warp call (`ch` marks the
+// lanes holding a changed node, `bal` is their ballot).
+__device__ __forceinline__ void tally_runs(const Plan &p, bool ch, unsigned bal, int32_t v,
+                                           uint32_t mask, MarkTally &mt)
 {
-    const bool ch = leader && mask != 0;
-    const unsigned bal = __ballot_sync(kFull, ch);
-    if (bal == 0) return;
     const int lane = threadIdx.x & 31;
-    if (lane == 0) mt.nodes += __popc(bal);
-    if (ch) atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
     if (p.K == 1) {
         // lane r counts run r: read the changed leaders' masks, or ballot
         // run by run, whichever takes fewer warp operations
@@ -378,6 +378,21 @@ __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, i
     }
 }
 
+// Record the nodes whose counters changed: the bitmap bit at once (a
+// fire-and-forget reduction), the counts in the tally.  Called by all lanes;
+// `leader` marks one lane per node, `mask` is its mask of changed runs.
+__device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, int32_t v,
+                                          uint32_t mask, MarkTally &mt)
+{
+    const bool ch = leader && mask != 0;
+    const unsigned bal = __ballot_sync(kFull, ch);
+    if (bal == 0) return;
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mt.nodes += __popc(bal);
+    if (ch) atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
+    tally_runs(p, ch, bal, v, mask, mt);
+}
+
 __device__ __forceinline__ unsigned warp_sum_u32(unsigned x)
 {
 #pragma unroll
@@ -391,6 +406,7 @@ __device__ __forceinline__ void flush_counters(const Plan &p, int cur, const Mar
 {
     const unsigned s0 = warp_sum_u32(scan), s1 = warp_sum_u32(gather);
     const unsigned s2 = warp_sum_u32(own), s3 = warp_sum_u32(write);
+    const unsigned nodes = mt.nodes + warp_sum_u32(mt.fresh);   // lane 0
     const int lane = threadIdx.x & 31;
     DevCtl *c = p.ctl;
     if (lane == 0) {
@@ -398,7 +414,7 @@ __device__ __forceinline__ void flush_counters(const Plan &p, int cur, const Mar
         if (s1) atomicAdd(&c->arcs_gathered, (unsigned long long)s1);
         if (s2) atomicAdd(&c->own_reads, (unsigned long long)s2);
         if (s3) atomicAdd(&c->writes, (unsigned long long)s3);
-        if (mt.nodes) atomicAdd(&c->changed_count[cur ^ 1], (unsigned long long)mt.nodes);
+        if (nodes) atomicAdd(&c->changed_count[cur ^ 1], (unsigned long long)nodes);
     }
     if (p.K == 1 && lane < p.R && mt.runs)
         atomicAdd(&p.slot_changed[lane], (unsigned long long)mt.runs);
@@ -418,7 +434,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
     constexpr int GPW = 32 / LANES;
     constexpr int U = 4 / VPL > 0 ? 4 / VPL : 1;
     const DevCtl *ctl = p.ctl;
-    if (ctl->done) return;
+    if (ctl->done || ctl->mode == kModeScatter) return;
     if constexpr (has_sparse_path<LANES, VPL>()) {
         if (SPARSE != (ctl->mode != kModeDense)) return;
     }
@@ -489,7 +505,7 @@ template <int LANES, int VPL>
 __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
 {
     const DevCtl *ctl = p.ctl;
-    if (ctl->done) return;
+    if (ctl->done || ctl->mode == kModeScatter) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
     const bool test = ctl->mode != kModeDense;
@@ -581,7 +597,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     static_assert(GPW * LANES == 32, "lane groups tile the warp");
     extern __shared__ uint4 smem_raw[];
     const DevCtl *ctl = p.ctl;
-    if (ctl->done) return;
+    if (ctl->done || ctl->mode == kModeScatter) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
     const bool test = ctl->mode != kModeDense;
@@ -713,7 +729,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
 {
     constexpr int GPW = 32 / LANES;
     const DevCtl *ctl = p.ctl;
-    if (ctl->done || p.n_hub == 0) return;
+    if (ctl->done || p.n_hub == 0 || ctl->mode == kModeScatter) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
     const bool push = ctl->mode == kModePush;
@@ -760,8 +776,13 @@ __global__ void k_prep(Plan p)
     if (c->done) return;
     const long long changed = (long long)c->last_changed;
     int mode = kModeTest;
+    const long long in_arcs = (long long)c->changed_in_arcs;
     if (c->t == 0 || p.frontier == HANF_FRONTIER_OFF)
         mode = kModeDense;
+    else if (p.frontier == HANF_FRONTIER_AUTO && p.in_off != nullptr && p.layout == 0 &&
+             p.scatter_den > 0 && in_arcs * p.scatter_den < p.arcs &&
+             in_arcs / p.scatter_seg + in_arcs / p.scatter_inline + 1 <= p.n)
+        mode = kModeScatter;   // the segment list fits the candidate lists
     else if (p.frontier == HANF_FRONTIER_AUTO && p.in_off != nullptr && changed * p.push_den < p.n)
         mode = kModePush;
     else if (p.in_off != nullptr
@@ -847,6 +868,282 @@ __global__ void k_mark(Plan p)
 
 // Slots (graph, run) that a pass left unchanged end at that pass (batches
 // with more than 8 slots; smaller ones are handled by k_post).
+// ---------------------------------------------------------------- scatter (pure push)
+
+// Scatter pass: Section 3.3's systolic computation carried to its end.  Once
+// the nodes changed by the last pass (F_t) have few in-arcs, every w in F_t
+// pushes c_t[w] into the new counter of each predecessor v, and nothing else
+// is visited.  Jacobi is kept: pushes read c_t (regs[p], untouched by the
+// pass) and raise c_{t+1} (regs[p^1]) with a compare-and-swap byte max, which
+// commutes, so the result does not depend on the order of the pushes.
+// regs[p^1] holds c_{t-1} on entry, which equals c_t except on F_t: those
+// rows are copied first (k_scatter_seed), before any push lands.
+__device__ __forceinline__ unsigned long long pack64(uint32_t lo, uint32_t hi)
+{
+    return (unsigned long long)lo | ((unsigned long long)hi << 32);
+}
+
+__device__ __forceinline__ unsigned long long bmax64(unsigned long long a, unsigned long long b)
+{
+    return pack64(bmax((uint32_t)a, (uint32_t)b), bmax((uint32_t)(a >> 32), (uint32_t)(b >> 32)));
+}
+
+// Raise the eight registers at q to at least those of `mine`.  `now` is a
+// value read from q earlier (possibly stale: registers only grow during the
+// pass, so a stale value is never above the current one).  Returns whether
+// this call raised q.  Every failed compare-and-swap means another thread
+// raised a register of q, which can happen at most 8 x 31 times, so the loop
+// always ends within its bound; `bad` records the impossible case.
+__device__ __forceinline__ bool raise64(unsigned long long *q, unsigned long long now,
+                                        unsigned long long mine, bool &bad)
+{
+    for (int it = 0; it <= 8 * 31; ++it) {
+        const unsigned long long want = bmax64(now, mine);
+        if (want == now) return false;
+        const unsigned long long seen = atomicCAS(q, now, want);
+        if (seen == now) return true;
+        now = seen;
+    }
+    bad = true;
+    return false;
+}
+
+// (node, predecessor) pairs a lane group of a scatter pass keeps in flight:
+// two rows of one vector a lane, one for wider lane rows.  (Four rows need
+// more than 80 registers; two resident blocks of 128 registers measured
+// slower than three of 80.)
+template <int LANES, int VPL>
+constexpr int kScatterRows = (LANES < 2 ? LANES : 2) / VPL > 0 ? (LANES < 2 ? LANES : 2) / VPL : 1;
+
+// Copy the rows of F_t into regs[p^1] (they hold c_{t-1} there) and cut the
+// in-arc lists longer than p.scatter_inline into segments, listed in
+// cand_list[0] (node) / cand_list[1] (segment index), counted in
+// cand_count[0].  A lane per changed node, a warp per bitmap word.
+__global__ void __launch_bounds__(kBlock) k_scatter_seed(Plan p)
+{
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done || ctl->mode != kModeScatter) return;
+    const int cur = ctl->parity;
+    const unsigned long long *Fc = p.F[cur];
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.regs[cur]);
+    uint4 *dst = reinterpret_cast<uint4 *>(p.regs[cur ^ 1]);
+    const int vec = p.W >> 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_write = 0;
+    bool bad = false;
+    for (int64_t i = warp; i < p.nwords; i += nwarps) {
+        const unsigned long long bits = Fc[i];
+        if (bits == 0ull) continue;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int bit = lane + 32 * h;
+            const int32_t w = (int32_t)(i * 64 + bit);
+            int32_t nseg = 0;
+            if ((bits >> bit) & 1ull) {
+#pragma unroll 4
+                for (int k = 0; k < vec; ++k) dst[(int64_t)w * vec + k] = src[(int64_t)w * vec + k];
+                ++c_write;
+                const int64_t d = p.in_off[w + 1] - p.in_off[w];
+                if (d > p.scatter_inline) nseg = (int32_t)((d + p.scatter_seg - 1) / p.scatter_seg);
+            }
+            int32_t incl = nseg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int32_t total = __shfl_sync(kFull, incl, 31);
+            if (total == 0) continue;
+            unsigned long long base = 0;
+            if (lane == 31) base = atomicAdd(&p.ctl->cand_count[0], (unsigned long long)total);
+            base = __shfl_sync(kFull, base, 31);
+            const unsigned long long first = base + (unsigned long long)(incl - nseg);
+            for (int32_t j = 0; j < nseg; ++j) {
+                if (first + j >= (unsigned long long)p.n) {   // k_prep's bound broken
+                    bad = true;
+                    break;
+                }
+                p.cand_list[0][first + j] = w;
+                p.cand_list[1][first + j] = j;
+            }
+        }
+    }
+    flush_counters(p, cur, MarkTally(), 0u, 0u, 0u, c_write);
+    if (bad) p.ctl->err = HANF_ESTATE;
+}
+
+// Push the (changed node w, predecessor v) pairs of up to 32 entries, one per
+// lane (entry: node w_l, its in-arcs [beg_l, beg_l + cnt_l)).  The entries'
+// pairs are numbered consecutively and taken 32 at a time, a pair per lane
+// (its entry found by binary search over the entries' prefix sums), so short
+// in-arc lists fill whole warps; lane group g then merges the pairs of lanes
+// g*LANES .. g*LANES+LANES-1, SUB rows in flight.  Warp-uniform control flow.
+template <int LANES, int VPL>
+__device__ __forceinline__ void scatter_entries(const Plan &p, int cur, int32_t w_l, int64_t beg_l,
+                                                int32_t cnt_l, MarkTally &mt, uint32_t &pairs,
+                                                uint32_t &raised, bool &bad)
+{
+    constexpr int SUB = kScatterRows<LANES, VPL>;
+    const int lane = threadIdx.x & 31, gl = lane % LANES, gbase = lane - gl;
+    const uint8_t *rc = p.regs[cur];
+    uint8_t *rn = p.regs[cur ^ 1];
+    int32_t incl = cnt_l;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int32_t total = __shfl_sync(kFull, incl, 31);
+    const int32_t excl = incl - cnt_l;
+    for (int32_t base = 0; base < total; base += 32) {
+        const int32_t q = base + lane;
+        // entry of pair q: the last lane whose prefix sum is <= q
+        int lo = 0;
+#pragma unroll
+        for (int st = 16; st; st >>= 1) {
+            const int32_t e = __shfl_sync(kFull, excl, lo + st);
+            if (e <= q) lo += st;
+        }
+        const int32_t w = __shfl_sync(kFull, w_l, lo);
+        const int64_t b = __shfl_sync(kFull, beg_l, lo);
+        const int32_t e0 = __shfl_sync(kFull, excl, lo);
+        const int32_t v = q < total ? __ldg(p.in_src + b + (q - e0)) : -1;
+#pragma unroll 1
+        for (int u0 = 0; u0 < LANES; u0 += SUB) {
+            int32_t ws[SUB], vs[SUB];
+#pragma unroll
+            for (int u = 0; u < SUB; ++u) {
+                ws[u] = __shfl_sync(kFull, w, gbase + u0 + u);
+                vs[u] = __shfl_sync(kFull, v, gbase + u0 + u);
+            }
+            Row<LANES, VPL> mine[SUB], now[SUB];
+#pragma unroll
+            for (int u = 0; u < SUB; ++u)
+                if (vs[u] >= 0) {
+                    row_load(mine[u], rc, ws[u], gl);
+                    const uint4 *qn = reinterpret_cast<const uint4 *>(rn) +
+                                      (int64_t)vs[u] * (LANES * VPL) + gl;
+#pragma unroll
+                    for (int k = 0; k < VPL; ++k) now[u].v[k] = __ldcg(qn + k * LANES);
+                }
+            // first attempts for every word of the round, all in flight
+            // together; the values they saw replace `now`, and fl[u] keeps,
+            // per 64-bit word i, bit 2i = raised, bit 2i+1 = retry needed
+            uint32_t fl[SUB];
+#pragma unroll
+            for (int u = 0; u < SUB; ++u) {
+                fl[u] = 0;
+                if (vs[u] >= 0) {
+                    unsigned long long *q64 = reinterpret_cast<unsigned long long *>(
+                        reinterpret_cast<uint4 *>(rn) + (int64_t)vs[u] * (LANES * VPL) + gl);
+#pragma unroll
+                    for (int k = 0; k < VPL; ++k) {
+                        const uint4 a = now[u].v[k], m4 = mine[u].v[k];
+                        const unsigned long long n0 = pack64(a.x, a.y), n1 = pack64(a.z, a.w);
+                        const unsigned long long w0 = bmax64(n0, pack64(m4.x, m4.y));
+                        const unsigned long long w1 = bmax64(n1, pack64(m4.z, m4.w));
+                        unsigned long long s0 = n0, s1 = n1;
+                        if (w0 != n0) s0 = atomicCAS(q64 + 2 * k * LANES, n0, w0);
+                        if (w1 != n1) s1 = atomicCAS(q64 + 2 * k * LANES + 1, n1, w1);
+                        if (w0 != n0) fl[u] |= (s0 == n0 ? 1u : 2u) << (4 * k);
+                        if (w1 != n1) fl[u] |= (s1 == n1 ? 1u : 2u) << (4 * k + 2);
+                        now[u].v[k] = make_uint4((uint32_t)s0, (uint32_t)(s0 >> 32), (uint32_t)s1,
+                                                 (uint32_t)(s1 >> 32));
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SUB; ++u) {
+                uint32_t mask = 0;
+                if (vs[u] >= 0) {
+                    unsigned long long *q64 = reinterpret_cast<unsigned long long *>(
+                        reinterpret_cast<uint4 *>(rn) + (int64_t)vs[u] * (LANES * VPL) + gl);
+#pragma unroll
+                    for (int k = 0; k < VPL; ++k) {
+                        const uint4 a = now[u].v[k], m4 = mine[u].v[k];
+                        bool r0 = (fl[u] >> (4 * k)) & 1u, r1 = (fl[u] >> (4 * k + 2)) & 1u;
+                        if ((fl[u] >> (4 * k + 1)) & 1u)   // lost a race: retry from what it saw
+                            r0 = raise64(q64 + 2 * k * LANES, pack64(a.x, a.y), pack64(m4.x, m4.y), bad);
+                        if ((fl[u] >> (4 * k + 3)) & 1u)
+                            r1 = raise64(q64 + 2 * k * LANES + 1, pack64(a.z, a.w), pack64(m4.z, m4.w),
+                                         bad);
+                        if (r0 || r1) mask |= 1u << (((k * LANES + gl) << 4) >> p.b);
+                    }
+                }
+                mask = group_or<LANES>(mask);
+                const bool ch = gl == 0 && vs[u] >= 0 && mask != 0;
+                const unsigned bal = __ballot_sync(kFull, ch);
+                if (bal) {
+                    if (ch) {
+                        const unsigned long long bit = 1ull << (vs[u] & 63);
+                        if ((atomicOr(&p.F[cur ^ 1][vs[u] >> 6], bit) & bit) == 0ull) ++mt.fresh;
+                    }
+                    tally_runs(p, ch, bal, vs[u], mask, mt);
+                }
+                if (gl == 0 && vs[u] >= 0) {
+                    ++pairs;
+                    if (mask) ++raised;
+                }
+            }
+        }
+    }
+}
+
+// The pushes of a scatter pass: a warp per item, items = the segments listed
+// by k_scatter_seed, then the bitmap words of F_t (their nodes of in-degree at
+// most p.scatter_inline, 32 entries at a time).
+template <int LANES, int VPL>
+__global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_scatter(Plan p)
+{
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done || ctl->mode != kModeScatter) return;
+    const int cur = ctl->parity;
+    const unsigned long long *Fc = p.F[cur];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nseg = min((int64_t)ctl->cand_count[0], p.n);   // the list's capacity
+    const int64_t total = nseg + p.nwords;
+    uint32_t pairs = 0, raised = 0;
+    MarkTally mt;
+    bool bad = false;
+    for (int64_t it = warp; it < total; it += nwarps) {
+        if (it < nseg) {
+            int32_t w = -1, cnt = 0;
+            int64_t beg = 0;
+            if (lane == 0) {
+                w = p.cand_list[0][it];
+                const int64_t j = p.cand_list[1][it];
+                const int64_t b0 = p.in_off[w], d = p.in_off[w + 1] - b0;
+                beg = b0 + j * p.scatter_seg;
+                cnt = (int32_t)min((int64_t)p.scatter_seg, d - j * p.scatter_seg);
+            }
+            scatter_entries<LANES, VPL>(p, cur, w, beg, cnt, mt, pairs, raised, bad);
+        } else {
+            const int64_t i = it - nseg;
+            const unsigned long long bits = Fc[i];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (((bits >> (32 * h)) & 0xffffffffull) == 0ull) continue;
+                const int bit = lane + 32 * h;
+                int32_t w = -1, cnt = 0;
+                int64_t beg = 0;
+                if ((bits >> bit) & 1ull) {
+                    w = (int32_t)(i * 64 + bit);
+                    beg = p.in_off[w];
+                    const int64_t d = p.in_off[w + 1] - beg;
+                    if (d <= p.scatter_inline) cnt = (int32_t)d;   // longer lists: by segments
+                }
+                scatter_entries<LANES, VPL>(p, cur, w, beg, cnt, mt, pairs, raised, bad);
+            }
+        }
+    }
+    flush_counters(p, cur, mt, pairs, pairs, pairs, raised);
+    if (bad) p.ctl->err = HANF_ESTATE;
+}
+
 __global__ void k_slot_T(Plan p)
 {
     const DevCtl *c = p.ctl;
@@ -862,12 +1159,14 @@ __global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
 {
     DevCtl *c = p.ctl;
     unsigned keep = 0;
-    if (!c->done) {
+    if (!c->done && c->err) {
+        c->done = 1;   // a scatter pass broke its bound: stop, the host reports it
+    } else if (!c->done) {
         const int nxt = c->parity ^ 1;
         const unsigned long long changed = c->changed_count[nxt];
         c->last_changed = changed;
         c->passes += 1;
-        if (c->mode == kModePush) c->push_passes += 1;
+        if (c->mode == kModePush || c->mode == kModeScatter) c->push_passes += 1;
         if (p.S <= 8)
             for (int r = 0; r < p.S; ++r)
                 if (p.slot_T[r] < 0 && p.slot_changed[r] == 0) p.slot_T[r] = c->t;
@@ -1874,6 +2173,15 @@ struct UnionKernels {
         const int64_t small_items = (p.n_small + GPW - 1) / GPW;
         const int blocks = (int)std::max<int64_t>(1, std::min(persistent, (warp_items + WPB - 1) / WPB));
         const int sblocks = (int)std::max<int64_t>(1, std::min(persistent, (small_items + WPB - 1) / WPB));
+        if (p.in_off && p.scatter_den > 0) {
+            // scatter passes (the kernels return at once in every other pass)
+            const int64_t scatter_items = p.nwords + p.n;   // words + at most n segments
+            k_scatter_seed<<<grid_for(p.nwords, WPB, 152 * 8), kBlock, 0, s>>>(p);
+            const int64_t spersistent = (p.scatter_warps * 32 + kBlock - 1) / kBlock;
+            k_scatter<LANES, VPL><<<(int)std::max<int64_t>(1, std::min(spersistent,
+                                                                        (scatter_items + WPB - 1) / WPB)),
+                                    kBlock, 0, s>>>(p);
+        }
         if constexpr (VPL == 1 && LANES <= 8) {
             if (p.warp_variant == 2) {
                 using Cfg = AsyncCfg<LANES>;
@@ -1897,6 +2205,12 @@ struct UnionKernels {
         const int blocks = grid_for((p.n_hub + GPW - 1) / GPW, kBlock / 32, 152 * 16);
         k_hub_finish<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
         return cudaGetLastError();
+    }
+    static int scatter_occupancy()
+    {
+        int a = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scatter<LANES, VPL>, kBlock, 0);
+        return a;
     }
     static int occupancy()
     {
@@ -1962,6 +2276,17 @@ int packed_occupancy_warps(int m, int nsm)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_punion_small<decltype(P)::value>, kBlock, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_punion_warp<decltype(P)::value>, kBlock, 0);
         nb = a < b ? a : b;
+        return cudaSuccess;
+    });
+    if (nb < 1) nb = 1;
+    return nb * nsm * (kBlock / 32);
+}
+
+int scatter_occupancy_warps(int W, int nsm)
+{
+    int nb = 0;
+    with_width(W, [&](auto k) {
+        nb = decltype(k)::scatter_occupancy();
         return cudaSuccess;
     });
     if (nb < 1) nb = 1;
@@ -2052,7 +2377,8 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
     if (nlaunch)
         *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
-                    (!p.layout && p.W <= 128 ? 1 : 0);
+                    (!p.layout && p.W <= 128 ? 1 : 0) +
+                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_estimate(p, s, nlaunch);
