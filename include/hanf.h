@@ -72,7 +72,8 @@ typedef struct hanf_opts {
     int32_t runs;          /* R >= 1 independent seeded runs batched together  */
     int32_t frontier;      /* HANF_FRONTIER_*; default AUTO                    */
     int32_t push_den;      /* systolic switch below n/push_den changes; 4      */
-    int32_t small_max_deg; /* degree <= this: a lane group per node; 0 = 256   */
+    int32_t small_max_deg; /* degree <= this: a lane group per node; 0 = 256,
+                              or 32 for rows of 512 bytes and more           */
     int32_t hub_min_deg;   /* degree > this: split in segments of this many
                               arcs, a warp each; 0 = 16384                     */
     int32_t history_cap;   /* capacity of the device N(t) history; 0 = 4096    */

@@ -46,6 +46,7 @@ int fail(int code, const char *fmt, ...)
     } while (0)
 
 constexpr int32_t kDefaultSmall = 256;    // hanf_autotune's choice on R-MAT scale 27 and 24
+constexpr int32_t kDefaultSmallWide = 32; // its choice for rows of 512 bytes and more (web-like, R = 8)
 constexpr int32_t kDefaultHub = 16384;
 constexpr int32_t kDefaultHistory = 4096;
 constexpr int64_t kStageRows = 65536;   // rows per chunk of a relabelled register read
@@ -120,7 +121,8 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
         s->W != 1024 && s->W != 2048)
         return fail(HANF_EINVAL, "runs * m = %d must be a power of two (runs 1, 2, 4 or 8)", s->W);
     if (o.layout == 1) s->W = 5 * s->m / 8;
-    s->d_small = o.small_max_deg ? o.small_max_deg : kDefaultSmall;
+    s->d_small = o.small_max_deg ? o.small_max_deg
+                                 : (o.layout == 0 && s->W >= 512 ? kDefaultSmallWide : kDefaultSmall);
     s->d_hub = o.hub_min_deg ? o.hub_min_deg : kDefaultHub;
     if (s->d_hub < 2) return fail(HANF_EINVAL, "hub_min_deg=%d < 2", s->d_hub);
     if (s->d_small > s->d_hub) s->d_small = s->d_hub;
@@ -246,6 +248,7 @@ struct hanf_ctx {
     int64_t launches;
     cudaGraphExec_t gexec;
     cudaStream_t capture_stream;
+    hanf::PassFork fork;         // side stream + events of the union launch
     std::vector<uint64_t> seeds;
     std::vector<double> trace;   // 8 values per pass (hanf_trace)
     const int32_t *perm;         // input id -> stored row (relabelled), or null
@@ -288,7 +291,7 @@ int one_pass(hanf_ctx *c)
     const DevCtl before = c->host_ctl;
     int nl = 0;
     CU(hanf::launch_pass(c->plan, c->stream, 0, 0, prof ? c->ev[0] : nullptr,
-                         prof ? c->ev[1] : nullptr, &nl));
+                         prof ? c->ev[1] : nullptr, &nl, &c->fork));
     c->launches += nl;
     int rc = read_ctl(c);
     if (rc) return rc;
@@ -329,7 +332,8 @@ int build_graph(hanf_ctx *c)
     CU(cudaStreamBeginCaptureToGraph(c->capture_stream, body, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
     int nl = 0;
-    cudaError_t le = hanf::launch_pass(c->plan, c->capture_stream, h, 1, nullptr, nullptr, &nl);
+    cudaError_t le = hanf::launch_pass(c->plan, c->capture_stream, h, 1, nullptr, nullptr, &nl,
+                                       &c->fork);
     cudaGraph_t captured = nullptr;
     cudaError_t ee = cudaStreamEndCapture(c->capture_stream, &captured);
     if (le != cudaSuccess || ee != cudaSuccess) {
@@ -427,6 +431,9 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     if (!c) return fail(HANF_ENOMEM, "host allocation failed");
     auto bail = [&](int code) {
         if (c->ev[0]) for (auto &e : c->ev) if (e) cudaEventDestroy(e);
+        if (c->fork.side) cudaStreamDestroy(c->fork.side);
+        if (c->fork.fork) cudaEventDestroy(c->fork.fork);
+        if (c->fork.join) cudaEventDestroy(c->fork.join);
         delete c;
         return code;
     };
@@ -440,6 +447,10 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
         return bail(fail(HANF_ECUDA, "no CUDA device"));
     for (auto &e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(HANF_ECUDA, "event create failed"));
+    if (cudaStreamCreateWithFlags(&c->fork.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork.join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(HANF_ECUDA, "side stream create failed"));
 
     uint8_t *ws = static_cast<uint8_t *>(workspace);
     Plan &p = c->plan;
@@ -1094,6 +1105,12 @@ void hanf_destroy(hanf_ctx *c)
     else cudaDeviceSynchronize();
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->fork.side) {
+        cudaStreamSynchronize(c->fork.side);
+        cudaStreamDestroy(c->fork.side);
+    }
+    if (c->fork.fork) cudaEventDestroy(c->fork.fork);
+    if (c->fork.join) cudaEventDestroy(c->fork.join);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     delete c;

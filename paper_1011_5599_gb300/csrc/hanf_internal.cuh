@@ -100,8 +100,15 @@ struct Plan {
 cudaError_t launch_validate(const Plan &p, cudaStream_t s);
 cudaError_t launch_init(const Plan &p, cudaStream_t s);
 cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch);
+// A second stream for the union kernels of one pass: the small-degree
+// kernel runs on `side` beside the warp kernel, joined before the hub combine.
+struct PassFork {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
 cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
-                        cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch);
+                        cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch,
+                        const PassFork *fk = nullptr);
 int union_occupancy_warps(int W, int nsm);
 int scatter_occupancy_warps(int W, int nsm);
 int packed_occupancy_warps(int m, int nsm);

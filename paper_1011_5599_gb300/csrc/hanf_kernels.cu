@@ -2162,7 +2162,7 @@ cudaError_t with_planes(int m, F &&f)
 
 template <int LANES, int VPL>
 struct UnionKernels {
-    static cudaError_t launch(const Plan &p, cudaStream_t s)
+    static cudaError_t launch(const Plan &p, cudaStream_t s, const PassFork *fk)
     {
         // persistent grids, but no larger than the work: small graphs launch
         // (and retire) only the blocks they can use
@@ -2182,6 +2182,15 @@ struct UnionKernels {
                                                                         (scatter_items + WPB - 1) / WPB)),
                                     kBlock, 0, s>>>(p);
         }
+        // the small-degree kernel runs on the side stream beside the warp
+        // kernel (disjoint nodes; bitmap bits and counts by atomics), so each
+        // fills the SMs the other drains
+        cudaStream_t ss = s;
+        if (fk && fk->side && p.W >= 128) {   // measured: a small loss at 64-byte rows
+            cudaEventRecord(fk->fork, s);
+            cudaStreamWaitEvent(fk->side, fk->fork, 0);
+            ss = fk->side;
+        }
         if constexpr (VPL == 1 && LANES <= 8) {
             if (p.warp_variant == 2) {
                 using Cfg = AsyncCfg<LANES>;
@@ -2194,9 +2203,13 @@ struct UnionKernels {
         } else {
             k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
         }
-        k_union_small<LANES, VPL, false><<<sblocks, kBlock, 0, s>>>(p);
+        k_union_small<LANES, VPL, false><<<sblocks, kBlock, 0, ss>>>(p);
         if constexpr (has_sparse_path<LANES, VPL>())
-            k_union_small<LANES, VPL, true><<<sblocks, kBlock, 0, s>>>(p);
+            k_union_small<LANES, VPL, true><<<sblocks, kBlock, 0, ss>>>(p);
+        if (ss != s) {
+            cudaEventRecord(fk->join, ss);
+            cudaStreamWaitEvent(s, fk->join, 0);
+        }
         return cudaGetLastError();
     }
     static cudaError_t launch_hub(const Plan &p, cudaStream_t s)
@@ -2345,7 +2358,7 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
 }
 
 cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
-                        cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch)
+                        cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch, const PassFork *fk)
 {
     k_prep<<<1, 1, 0, s>>>(p);
     k_clear<<<grid_for(std::max<int64_t>(p.nwords, p.S), kBlock, 152 * 16), kBlock, 0, s>>>(p);
@@ -2367,7 +2380,7 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
             return cudaGetLastError();
         });
     } else {
-        err = with_width(p.W, [&](auto k) { return decltype(k)::launch(p, s); });
+        err = with_width(p.W, [&](auto k) { return decltype(k)::launch(p, s, fk); });
         if (err == cudaSuccess && p.n_hub)
             err = with_width(p.W, [&](auto k) { return decltype(k)::launch_hub(p, s); });
     }

@@ -131,3 +131,27 @@ def test_scatter_batch_of_graphs(H, oracle, R):
             assert T[s] == To, (g, r)
             np.testing.assert_allclose(N[s], No, rtol=RTOL, atol=0)
             assert np.array_equal(regs[g][r], ro), (g, r)
+
+
+def sinks_graph(n=1 << 18, arcs=1 << 21, seed=3):
+    """Half of the nodes have no out-arcs (they are left out of the degree-
+    class lists); the other half point anywhere, so sinks are targets too."""
+    rng = np.random.default_rng(seed)
+    src = rng.integers(0, n // 2, arcs)
+    dst = rng.integers(0, n, arcs)
+    return G.csr_from_arcs(src, dst, n)
+
+
+@pytest.mark.parametrize("scatter_den", [1, -1])
+def test_transpose_with_sinks_and_a_dirty_workspace(H, oracle, scatter_den):
+    """The transpose behind systolic and scatter passes must not depend on what
+    the workspace held before: fill the allocator's cache with valid-looking
+    node ids first, then run with many arc-less nodes."""
+    import torch
+    off, tgt = sinks_graph()
+    n = off.size - 1
+    junk = torch.randint(0, n, (1 << 28,), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    del junk          # the caching allocator hands this block out again
+    run_and_check(H, oracle, off, tgt, 6, expect_scatter=scatter_den > 0,
+                  scatter_den=scatter_den)
