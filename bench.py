@@ -145,11 +145,13 @@ def gpu_index_for(device):
 
 # ------------------------------------------------------------------ profile summary
 
-def ncu_traffic(workload):
+def ncu_traffic(workload, layout="byte"):
     """Per-launch DRAM bytes of the union kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+    summary of this workload and register layout, or None when there is none
+    or the kernel source changed since the capture."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"union_{workload}.md")
+    suffix = "" if layout == "byte" else f"_{layout}"
+    path = os.path.join(ROOT, "profiles", f"union_{workload}{suffix}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -579,10 +581,10 @@ def main():
     peak, peak_kind = measured_peak()
     steps_passes = sum(passes_list)
     achieved = union_bytes / (union_ms / 1e3) / 1e9 if union_ms > 0 else None
-    traffic = ncu_traffic(args.workload)
+    traffic = ncu_traffic(args.workload, args.layout)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_union (+ k_hub_finish)",
+            "traffic": traffic, "peak_kind": peak_kind, "kernel": "union launches of one pass (k_union_*, k_scatter*, k_hub_finish)",
             "algorithmic_bytes_per_launch": union_bytes / max(steps_passes, 1),
             "avg_launch_ms": union_ms / max(steps_passes, 1)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
