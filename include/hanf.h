@@ -172,14 +172,19 @@ HANF_API int hanf_current_t(hanf_ctx *ctx, int32_t *t_out);
  * counters read), out[3] own counters read, out[4] counters written,
  * out[5] union-kernel launches, out[6] union-kernel milliseconds (profile = 1,
  * else 0), out[7] all kernel launches, out[8] estimator milliseconds,
- * out[9] passes run in systolic (push) mode.  nout = entries wanted (<= 10). */
+ * out[9] passes run in systolic or scatter (push) mode.  In scatter passes
+ * "arcs scanned" and "arcs gathered" count the (changed node, predecessor)
+ * pairs pushed, "own counters read" the rows read to push into, and
+ * "counters written" the rows copied or raised.  nout = entries wanted
+ * (<= 10). */
 HANF_API int hanf_counters(hanf_ctx *ctx, double *out, int32_t nout);
 
 /* Per-pass trace of the last run since initialisation (profile = 1 and the
  * host-loop driver): up to max_rows rows of 8 doubles {t, mode (0 pull with
  * the changed-bitmap test, 1 systolic push, 2 pull gathering every
- * successor), nodes changed, union milliseconds, arcs scanned, arcs gathered,
- * own counters read, counters written}; *rows_out = rows written. */
+ * successor, 3 scatter: changed nodes push into their predecessors), nodes
+ * changed, union milliseconds, arcs scanned, arcs gathered, own counters
+ * read, counters written}; *rows_out = rows written. */
 HANF_API int hanf_trace(hanf_ctx *ctx, double *out, int32_t max_rows, int32_t *rows_out);
 
 /* Section 4 and 5 statistics of N(0..T) (host arrays, no GPU):
