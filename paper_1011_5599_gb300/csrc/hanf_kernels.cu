@@ -1189,29 +1189,35 @@ __global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
 // ---------------------------------------------------------------- estimator
 
 // size() of run r of node v (Algorithm 1 with linear counting).  The sum of
-// 2^-M[j] is exact: it is accumulated as the integer sum of 2^(31-M[j]).
+// 2^-M[j] is exact: it is accumulated as the integer sum of 2^(31-M[j]).  M
+// registers a run, known at compile time so that a lane issues all of its
+// loads before it adds; zero registers are counted a 32-bit word at a time
+// (with the registers below 32, bit 7 of each byte is free: after setting it,
+// subtracting 1 per byte clears it exactly in the bytes that were 0).
+template <int M>
 __device__ __forceinline__ double node_size(const Plan &p, const uint8_t *rc, int64_t v, int r)
 {
-    const uint4 *q = reinterpret_cast<const uint4 *>(rc + v * p.W + (int64_t)r * p.m);
+    const uint4 *q = reinterpret_cast<const uint4 *>(rc + v * p.W + (int64_t)r * M);
+    uint4 x[M / 16];
+#pragma unroll
+    for (int k = 0; k < M / 16; ++k) x[k] = q[k];
     unsigned long long S = 0;
     int V = 0;
-    for (int k = 0; k < (p.m >> 4); ++k) {
-        const uint4 x = q[k];
-        const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < M / 16; ++k) {
+        const uint32_t w4[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+            const uint32_t z = (w4[j] | 0x80808080u) - 0x01010101u;
+            V += __popc(~z & 0x80808080u);
 #pragma unroll
-            for (int s = 0; s < 32; s += 8) {
-                const uint32_t M = (w4[j] >> s) & 0xffu;
-                S += 1ull << (31 - M);
-                V += M == 0;
-            }
+            for (int s = 0; s < 32; s += 8) S += 0x80000000u >> ((w4[j] >> s) & 0xffu);
         }
     }
     const double sum = (double)S * 0x1p-31;
     const double Z = 1.0 / sum;
     double E = p.amm * Z;
-    if (E <= 2.5 * (double)p.m && V > 0) E = p.lc[V];
+    if (E <= 2.5 * (double)M && V > 0) E = p.lc[V];
     return E;
 }
 
@@ -1251,6 +1257,7 @@ __device__ __forceinline__ void node_stats_update(const Plan &p, int r, int64_t 
 // partial sums of small blocks).  A warp per (run, block); the warp sum uses
 // a fixed butterfly, so the partial is a deterministic function of the
 // block's registers.
+template <int M>
 __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
 {
     DevCtl *c = p.ctl;
@@ -1284,8 +1291,8 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
             const int g = __ldg(p.blk_graph + blk);
             lim = p.g_base[g] + p.g_nodes[g];
         }
-        const double e0 = v0 < lim ? node_size(p, rc, v0, r) : 0.0;
-        const double e1 = v1 < lim ? node_size(p, rc, v1, r) : 0.0;
+        const double e0 = v0 < lim ? node_size<M>(p, rc, v0, r) : 0.0;
+        const double e1 = v1 < lim ? node_size<M>(p, rc, v1, r) : 0.0;
         if (p.node_stats) {
             if (v0 < lim) node_stats_update(p, r, v0, e0, all, c->t);
             if (v1 < lim) node_stats_update(p, r, v1, e1, all, c->t);
@@ -2344,7 +2351,15 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
         });
         if (err != cudaSuccess) return err;
     } else {
-        k_est_blocks<<<grid_for(p.nwords * p.R, kBlock / 32, 152 * 64), kBlock, 0, s>>>(p);
+        const int g = grid_for(p.nwords * p.R, kBlock / 32, 152 * 64);
+        switch (p.m) {
+        case 16: k_est_blocks<16><<<g, kBlock, 0, s>>>(p); break;
+        case 32: k_est_blocks<32><<<g, kBlock, 0, s>>>(p); break;
+        case 64: k_est_blocks<64><<<g, kBlock, 0, s>>>(p); break;
+        case 128: k_est_blocks<128><<<g, kBlock, 0, s>>>(p); break;
+        case 256: k_est_blocks<256><<<g, kBlock, 0, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     if (p.K > 1) {
         k_est_reduce_graphs<<<p.S, kBlock, 0, s>>>(p);

@@ -155,3 +155,24 @@ def test_transpose_with_sinks_and_a_dirty_workspace(H, oracle, scatter_den):
     del junk          # the caching allocator hands this block out again
     run_and_check(H, oracle, off, tgt, 6, expect_scatter=scatter_den > 0,
                   scatter_den=scatter_den)
+
+
+@pytest.mark.parametrize("log2m,R", [(4, 1), (7, 1), (6, 8), (8, 8)])
+def test_degenerate_graphs_every_flavour(H, oracle, log2m, R):
+    """Empty and arc-less graphs, a single node, self-loops and duplicate arcs,
+    with scatter passes forced, with them off, and with the pull frontier,
+    at rows of 16 to 2048 bytes (the widest also use the second stream)."""
+    loops = (np.array([0, 3, 5, 6, 6], dtype=np.int64), np.array([0, 1, 1, 2, 2, 0], dtype=np.int32))
+    one_arc = (np.array([0, 1, 1], dtype=np.int64), np.array([1], dtype=np.int32))
+    graphs = [G.empty(0), G.empty(1), G.empty(65), loops, one_arc, G.path(3), G.star(70)]
+    for off, tgt in graphs:
+        for kw in (dict(scatter_den=1), dict(scatter_den=-1), dict(frontier="pull")):
+            with H.HyperANF(off, tgt, log2m, SEED, runs=R, **kw) as h:
+                N, T = h.run()
+                regs = [h.registers(r) for r in range(R)]
+            for r in range(R):
+                No, To, ro = oracle.hyperanf(off, tgt, log2m, oracle.run_seed(SEED, r),
+                                             want_regs=True)
+                assert T[r] == To, (off.size - 1, kw, r)
+                assert np.array_equal(regs[r], ro), (off.size - 1, kw, r)
+                np.testing.assert_allclose(N[r], No, rtol=RTOL, atol=0)
