@@ -55,7 +55,7 @@ WORKLOADS = {
                text="directed ER n=10^4, 5*10^4 arcs, m=16, 1 run"),
 }
 # bounded CPU samples of the same recipes for the oracle
-CPU_SAMPLE = {"rmat27": dict(kind="rmat", scale=21, ef=16, sym=False),
+CPU_SAMPLE = {"rmat27": dict(kind="rmat", scale=22, ef=16, sym=False),
               "rmat22": dict(kind="rmat", scale=18, ef=16, sym=False),
               "rmat24": dict(kind="rmat", scale=19, ef=16, sym=False),
               "rmat24sym": dict(kind="rmat", scale=18, ef=16, sym=True),

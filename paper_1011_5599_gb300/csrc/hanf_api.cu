@@ -447,7 +447,9 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
         return bail(fail(HANF_ECUDA, "no CUDA device"));
     for (auto &e : c->ev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(HANF_ECUDA, "event create failed"));
-    if (cudaStreamCreateWithFlags(&c->fork.side, cudaStreamNonBlocking) != cudaSuccess ||
+    int prio = 0;   // the side stream runs at the priority of the context's stream
+    if (cudaStreamGetPriority(c->stream, &prio) != cudaSuccess) prio = 0;
+    if (cudaStreamCreateWithPriority(&c->fork.side, cudaStreamNonBlocking, prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork.join, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(HANF_ECUDA, "side stream create failed"));

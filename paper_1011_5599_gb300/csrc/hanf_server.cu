@@ -7,6 +7,9 @@
 // allocation, coalescing free list): the admitted job's context is created in
 // its slice of the arena and the whole of Algorithm 2 runs as one CUDA graph
 // on the worker's stream, so jobs of different workers overlap on the GPU.
+// Streams carry priorities in arrival order: a job admitted while others run
+// ranks below them, so the oldest job runs nearly as if alone and newer jobs
+// use the SMs it leaves free.
 // Each job has its own context, so its result does not depend on what else is
 // running.  hanf_server_wait returns a job's N(t), T and timings.
 #include <cuda_runtime.h>
@@ -109,7 +112,10 @@ struct hanf_server {
     std::deque<std::shared_ptr<Job>> queue;
     std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
     std::vector<std::thread> workers;
-    std::vector<cudaStream_t> streams;
+    // streams[w][k]: worker w's stream at priority level k (0 = highest)
+    std::vector<std::vector<cudaStream_t>> streams;
+    int prio_greatest = 0, levels = 1;
+    int next_level = 0;            // level of the next admitted job (arrival order)
     uint64_t next_id = 1;
     bool stopping = false;
     int running = 0;
@@ -169,10 +175,10 @@ void run_job(hanf_server *s, Job &job, uint8_t *ws, cudaStream_t st)
 void worker_main(hanf_server *s, int w)
 {
     cudaSetDevice(s->device);
-    cudaStream_t st = s->streams[w];
     for (;;) {
         std::shared_ptr<Job> job;
         size_t off = 0;
+        cudaStream_t st = nullptr;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
@@ -188,6 +194,12 @@ void worker_main(hanf_server *s, int w)
             }
             job->status = 2;
             job->t_start = Clock::now();
+            // jobs admitted while others run get lower priorities, in arrival
+            // order: the oldest job's blocks are scheduled first, the newer
+            // ones fill the SMs it leaves free; an idle GPU starts over
+            if (s->running == 0) s->next_level = 0;
+            st = s->streams[w][std::min(s->next_level, s->levels - 1)];
+            ++s->next_level;
             ++s->running;
         }
         run_job(s, *job, s->arena + off, st);
@@ -226,14 +238,21 @@ int hanf_server_create(hanf_server **out, void *arena, size_t arena_bytes, int32
         delete s;
         return server_fail(HANF_ECUDA, "no CUDA device");
     }
-    s->streams.resize(workers);
-    for (int w = 0; w < workers; ++w) {
-        if (cudaStreamCreateWithFlags(&s->streams[w], cudaStreamNonBlocking) != cudaSuccess) {
-            for (int k = 0; k < w; ++k) cudaStreamDestroy(s->streams[k]);
-            delete s;
-            return server_fail(HANF_ECUDA, "stream creation failed");
-        }
-    }
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+    s->prio_greatest = greatest;
+    s->levels = least - greatest + 1;
+    s->streams.assign(workers, std::vector<cudaStream_t>(s->levels, nullptr));
+    for (int w = 0; w < workers; ++w)
+        for (int k = 0; k < s->levels; ++k)
+            if (cudaStreamCreateWithPriority(&s->streams[w][k], cudaStreamNonBlocking,
+                                             greatest + k) != cudaSuccess) {
+                for (auto &row : s->streams)
+                    for (cudaStream_t x : row)
+                        if (x) cudaStreamDestroy(x);
+                delete s;
+                return server_fail(HANF_ECUDA, "stream creation failed");
+            }
     for (int w = 0; w < workers; ++w) s->workers.emplace_back(worker_main, s, w);
     *out = s;
     return HANF_OK;
@@ -342,7 +361,8 @@ void hanf_server_destroy(hanf_server *s)
     s->cv_work.notify_all();
     s->cv_done.notify_all();
     for (auto &t : s->workers) t.join();
-    for (auto st : s->streams) cudaStreamDestroy(st);
+    for (auto &row : s->streams)
+        for (cudaStream_t st : row) cudaStreamDestroy(st);
     delete s;
 }
 
