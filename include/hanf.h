@@ -216,8 +216,10 @@ HANF_API int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2m,
 /* Autotuner (the paper has no counterpart; its thread pool needs no tuning):
  * times candidate launch parameters of the union pass on this graph -- the
  * degree split small_max_deg in {32,128,256,1024,4096}, hub_min_deg in
- * {4096,16384,65536} and gather_variant in {1,2} -- each with its own
- * context in `workspace`,
+ * {4096,16384,65536} and gather_variant in {1,2}, then on the best of those
+ * (frontier AUTO, byte layout, scatter_den 0 in *base) the pass flavour the
+ * row width does not default to (scatter_den -1 for rows up to 128 bytes, 8
+ * above) -- each with its own context in `workspace`,
  * one warm-up and one timed run of Algorithm 2, and returns the fastest in
  * *best_out (the other fields copied from *base, NULL = defaults) and its
  * time in *best_ms_out (nullable).  cache_path (nullable) names a text file:

@@ -1,7 +1,8 @@
 // Autotuner: picks the launch parameters of the union pass for one graph by
 // timing them.  The tuned knobs are the degree split (small_max_deg: nodes
-// per lane group vs per warp; hub_min_deg: segment length of hub nodes) and
-// the gather variant of the warp kernel.  Each candidate gets its own context
+// per lane group vs per warp; hub_min_deg: segment length of hub nodes), the
+// gather variant of the warp kernel and, as a second stage on the best of
+// those, whether late passes push (scatter) or pull (systolic).  Each candidate gets its own context
 // in the caller's workspace, one untimed warm-up run and one timed run of the
 // whole of Algorithm 2; the fastest wins.  Results are remembered in a text
 // cache (one "key value..." line per tuned shape) so that later calls with the
@@ -47,7 +48,7 @@ std::string shape_key(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o
 }
 
 bool cache_lookup(const char *path, const std::string &key, int32_t *small, int32_t *hub,
-                  int32_t *variant, double *ms)
+                  int32_t *variant, int32_t *scatter, double *ms)
 {
     if (!path) return false;
     std::ifstream in(path);
@@ -56,12 +57,13 @@ bool cache_lookup(const char *path, const std::string &key, int32_t *small, int3
     while (std::getline(in, line)) {   // the last entry for a key wins
         std::istringstream ss(line);
         std::string k;
-        int32_t a, b, c;
+        int32_t a, b, c, d;
         double t;
-        if ((ss >> k >> a >> b >> c >> t) && k == key) {
+        if ((ss >> k >> a >> b >> c >> d >> t) && k == key) {
             *small = a;
             *hub = b;
             *variant = c;
+            *scatter = d;
             *ms = t;
             found = true;
         }
@@ -84,24 +86,53 @@ extern "C" int hanf_autotune(int64_t n, int64_t arcs, const int64_t *offsets,
     o.use_graph = 1;
     o.profile = 0;
     const std::string key = shape_key(n, arcs, log2m, o);
-    int32_t cs, ch, cv;
+    int32_t cs, ch, cv, cd;
     double cms;
-    if (cache_lookup(cache_path, key, &cs, &ch, &cv, &cms)) {
+    if (cache_lookup(cache_path, key, &cs, &ch, &cv, &cd, &cms)) {
         *best_out = o;
         best_out->small_max_deg = cs;
         best_out->hub_min_deg = ch;
         best_out->gather_variant = cv;
+        best_out->scatter_den = cd;
         if (best_ms_out) *best_ms_out = cms;
         return HANF_OK;
     }
-    const int32_t smalls[] = {32, 128, 256, 1024, 4096};
-    const int32_t hubs[] = {4096, 16384, 65536};
-    const int32_t variants[] = {1, 2};
     double best_ms = INFINITY;
     hanf_opts best = o;
     std::vector<double> N(4096 * (size_t)std::max(o.runs, 1));
     std::vector<int32_t> T(std::max(o.runs, 1));
     cudaStream_t st = static_cast<cudaStream_t>(o.stream);
+    // one candidate: a context, an untimed warm-up run, a timed run; returns
+    // a status (a candidate that does not fit the workspace is skipped)
+    auto trial = [&](const hanf_opts &c) -> int {
+        size_t need = 0;
+        int rc = hanf_workspace_size(n, arcs, log2m, &c, graph_on_device ? 0 : 1, &need);
+        if (rc) return rc;
+        if (need > workspace_bytes) return HANF_OK;
+        hanf_ctx *ctx = nullptr;
+        rc = hanf_create(&ctx, n, arcs, offsets, targets, graph_on_device, log2m, seed, &c,
+                         workspace, workspace_bytes);
+        if (rc) return rc;
+        rc = hanf_run(ctx, 4096, N.data(), 4096, T.data());
+        if (rc == HANF_OK) {
+            if (st) cudaStreamSynchronize(st);
+            else cudaDeviceSynchronize();
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = hanf_run(ctx, 4096, N.data(), 4096, T.data());
+            const double ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                    .count();
+            if (rc == HANF_OK && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        hanf_destroy(ctx);
+        return rc;
+    };
+    const int32_t smalls[] = {32, 128, 256, 1024, 4096};
+    const int32_t hubs[] = {4096, 16384, 65536};
+    const int32_t variants[] = {1, 2};
     for (int32_t vsm : smalls)
         for (int32_t vh : hubs)
             for (int32_t gv : variants) {
@@ -110,37 +141,24 @@ extern "C" int hanf_autotune(int64_t n, int64_t arcs, const int64_t *offsets,
                 c.small_max_deg = vsm;
                 c.hub_min_deg = vh;
                 c.gather_variant = gv;
-                size_t need = 0;
-                int rc = hanf_workspace_size(n, arcs, log2m, &c, graph_on_device ? 0 : 1, &need);
-                if (rc) return rc;
-                if (need > workspace_bytes) continue;
-                hanf_ctx *ctx = nullptr;
-                rc = hanf_create(&ctx, n, arcs, offsets, targets, graph_on_device, log2m, seed, &c,
-                                 workspace, workspace_bytes);
-                if (rc) return rc;
-                rc = hanf_run(ctx, 4096, N.data(), 4096, T.data());
-                if (rc == HANF_OK) {
-                    if (st) cudaStreamSynchronize(st);
-                    else cudaDeviceSynchronize();
-                    const auto t0 = std::chrono::steady_clock::now();
-                    rc = hanf_run(ctx, 4096, N.data(), 4096, T.data());
-                    const double ms = std::chrono::duration<double, std::milli>(
-                                          std::chrono::steady_clock::now() - t0)
-                                          .count();
-                    if (rc == HANF_OK && ms < best_ms) {
-                        best_ms = ms;
-                        best = c;
-                    }
-                }
-                hanf_destroy(ctx);
+                const int rc = trial(c);
                 if (rc) return rc;
             }
+    // stage 2 on the best split: the pass flavour the row width does not
+    // default to (pushes for rows up to 128 bytes, pulls for wider ones)
+    if (std::isfinite(best_ms) && o.frontier == HANF_FRONTIER_AUTO && !o.layout &&
+        o.scatter_den == 0) {
+        hanf_opts c = best;
+        c.scatter_den = (1 << log2m) * o.runs <= 128 ? -1 : 8;
+        const int rc = trial(c);
+        if (rc) return rc;
+    }
     if (!std::isfinite(best_ms))
         return tune_fail(HANF_ENOMEM, "no candidate fits in the workspace");
     if (cache_path) {
         std::ofstream out(cache_path, std::ios::app);
         out << key << ' ' << best.small_max_deg << ' ' << best.hub_min_deg << ' '
-            << best.gather_variant << ' ' << best_ms << '\n';
+            << best.gather_variant << ' ' << best.scatter_den << ' ' << best_ms << '\n';
     }
     *best_out = best;
     if (best_ms_out) *best_ms_out = best_ms;

@@ -452,7 +452,8 @@ class HyperANF:
 def autotune(offsets, targets, log2m: int, seed: int = 0x5EED, cache_path=None, device=None,
              **opts) -> tuple[dict, float]:
     """hanf_autotune on a graph; returns ({small_max_deg, hub_min_deg,
-    gather_variant}, best ms).  ``offsets``/``targets`` as for HyperANF."""
+    gather_variant, scatter_den}, best ms).  ``offsets``/``targets`` as for
+    HyperANF."""
     import torch
 
     device = torch.device(device if device is not None else "cuda")
@@ -476,7 +477,7 @@ def autotune(offsets, targets, log2m: int, seed: int = 0x5EED, cache_path=None, 
                               ctypes.byref(base), ws.data_ptr(), size, path, ctypes.byref(best),
                               ctypes.byref(ms)))
     return ({"small_max_deg": best.small_max_deg, "hub_min_deg": best.hub_min_deg,
-             "gather_variant": best.gather_variant}, ms.value)
+             "gather_variant": best.gather_variant, "scatter_den": best.scatter_den}, ms.value)
 
 
 class Server:
