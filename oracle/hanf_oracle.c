@@ -27,7 +27,13 @@
  * rho+, closed-form size() cases, exact ball registers by breadth-first
  * search, the closed-form neighbourhood functions (Section 4 counterexample;
  * paths, cycles, stars, complete digraphs), Theorem 1 / Vysochanskii-Petunin
- * bands over seeds, and closed-form distance statistics.
+ * bands over seeds, closed-form distance statistics, Algorithm 3 brackets of
+ * exact effective diameters, and per-node eccentricity / distance-sum bounds
+ * against breadth-first search.
+ *
+ * Parity unpinned: the spid and effective-diameter values the paper measures
+ * on its datasets (Table 2) -- the datasets are absent, so these statistics
+ * are pinned only through their definitions on exact distributions.
  */
 #include <stdint.h>
 #include <stdlib.h>
