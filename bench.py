@@ -434,7 +434,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
-    ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2])
+    ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2, 3])
     ap.add_argument("--scatter-den", type=int, default=0,
                     help="pure-push passes below arcs/scatter_den changed in-arcs (0 = library "
                          "default, negative = never)")

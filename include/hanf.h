@@ -87,10 +87,14 @@ typedef struct hanf_opts {
     int32_t relabel;       /* 1 = store the counters in decreasing in-degree
                               order (hot counters share cache lines); results
                               and hanf_registers use input ids either way    */
-    int32_t gather_variant;/* medium-degree nodes and hub segments gather rows
-                              with 0 = the default, 1 = register batches,
-                              2 = asynchronous copies into a shared-memory
-                              ring (rows of at most 128 bytes)                */
+    int32_t gather_variant;/* how rows are gathered: 1 = register batches in
+                              every kernel; 2 = asynchronous copies into a
+                              shared-memory ring for medium-degree nodes and
+                              hub segments; 3 = asynchronous copies into
+                              per-lane shared-memory slots in the small-degree
+                              kernel's dense passes; 0 = the default, 3 for
+                              rows of at most 128 bytes (2 and 3 apply to such
+                              rows only), 1 otherwise                         */
     int32_t layout;        /* 0 = one byte per register; 1 = five bit-planes of
                               m bits (5m/8 bytes per counter; runs = 1 and
                               m >= 32); results are identical               */
@@ -216,7 +220,8 @@ HANF_API int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2m,
 /* Autotuner (the paper has no counterpart; its thread pool needs no tuning):
  * times candidate launch parameters of the union pass on this graph -- the
  * degree split small_max_deg in {32,128,256,1024,4096}, hub_min_deg in
- * {4096,16384,65536} and gather_variant in {1,2}, then on the best of those
+ * {4096,16384,65536} and gather_variant in {1,2,3} (2 and 3 for rows of at
+ * most 128 bytes), then on the best of those
  * (frontier AUTO, byte layout, scatter_den 0 in *base) the pass flavour the
  * row width does not default to (scatter_den -1 for rows up to 128 bytes, 8
  * above) -- each with its own context in `workspace`,

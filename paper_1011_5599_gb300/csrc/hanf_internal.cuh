@@ -93,6 +93,7 @@ struct Plan {
     int32_t scatter_warps;            // resident warps of the scatter launch
     int32_t union_async_warps;        // resident warps of the asynchronous-copy variant
     int32_t warp_variant;             // medium/hub gathers: 1 register batches, 2 async copies
+    int32_t small_variant;            // small-degree dense gathers: 0 registers, 3 async copies
     DevCtl *ctl;
 };
 
@@ -110,6 +111,7 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
                         cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch,
                         const PassFork *fk = nullptr);
 int union_occupancy_warps(int W, int nsm);
+int small_async_blocks(int W);
 int scatter_occupancy_warps(int W, int nsm);
 int packed_occupancy_warps(int m, int nsm);
 int union_async_warps(int W, int nsm);

@@ -722,6 +722,125 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
 }
 
+// Small-degree union with asynchronous row copies (gather_variant 3; rows of
+// at most 128 bytes, dense passes): each lane copies its 16-byte share of a
+// batch of UA rows into its own shared-memory slots with cp.async and merges
+// the previous batch meanwhile, so a lane group keeps up to 2 x UA rows in
+// flight without holding them in registers.  A lane only ever reads the
+// slots it filled itself, so cp.async.wait_group is the only wait (no
+// cross-lane barrier); rows a batch does not use are zero-filled, which
+// leaves the max unchanged.
+template <int LANES>
+struct SmallAsyncCfg {
+    static constexpr int UA = 8;                                        // rows per batch
+    static constexpr size_t smem_per_warp = 2 * (size_t)UA * 32 * sizeof(uint4);
+    static constexpr size_t smem_per_block = smem_per_warp * (kBlock / 32);
+};
+
+template <int LANES>
+__global__ void __launch_bounds__(kBlock, 3) k_union_small_async(Plan p)
+{
+    constexpr int GPW = 32 / LANES;
+    constexpr int UA = SmallAsyncCfg<LANES>::UA;
+    constexpr int TPL = (UA + LANES - 1) / LANES;
+    extern __shared__ uint4 async_rows[];
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done || ctl->mode != kModeDense) return;
+    const int cur = ctl->parity;
+    const bool first = ctl->t == 0;
+    const uint8_t *rc = p.regs[cur];
+    const unsigned long long *Fc = p.F[cur];
+    const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
+    const int gbase = g * LANES;
+    const unsigned gmask = ((1u << LANES) - 1u) << gbase;
+    uint4 *ring = async_rows + (size_t)(threadIdx.x >> 5) * (2 * UA * 32);
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
+    const int32_t *list = p.nodes;
+    const int64_t count = p.n_small;
+    const int64_t stride = nwarps * GPW;
+    int64_t idx_ahead = warp * GPW + g;
+    int32_t v_next = idx_ahead < count ? __ldg(list + idx_ahead) : -1;
+    int64_t beg_next = v_next >= 0 ? __ldg(p.off + v_next) : 0;
+    int64_t end_next = v_next >= 0 ? __ldg(p.off + v_next + 1) : 0;
+    idx_ahead += stride;
+    int32_t v_after = idx_ahead < count ? __ldg(list + idx_ahead) : -1;
+    // targets of a batch at e: each lane its TPL share
+    auto load_targets = [&](int32_t (&t)[TPL], int64_t e, int64_t end) {
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            const int j = gl + k * LANES;
+            t[k] = (j < UA && e + j < end) ? __ldg(p.tgt + e + j) : -1;
+        }
+    };
+    // copy the batch's rows into stage `st`: lane gl copies bytes
+    // [16 gl, 16 gl + 16) of each row; every lane of the warp takes part
+    auto issue = [&](const int32_t (&t)[TPL], int st) {
+#pragma unroll
+        for (int u = 0; u < UA; ++u) {
+            const int32_t w = __shfl_sync(kFull, t[u / LANES], gbase + (u % LANES));
+            const uint8_t *src = w >= 0 ? rc + (int64_t)w * (16 * LANES) + gl * 16 : rc;
+            cp_async16(ring + (st * UA + u) * 32 + lane, src, w >= 0);
+        }
+        cp_async_commit();
+    };
+    for (int64_t base = warp * GPW; base < count; base += stride) {
+        const int32_t v = v_next;
+        const int64_t beg = beg_next, end = end_next;
+        const bool valid = v >= 0;
+        v_next = v_after;
+        beg_next = v_next >= 0 ? __ldg(p.off + v_next) : 0;
+        end_next = v_next >= 0 ? __ldg(p.off + v_next + 1) : 0;
+        idx_ahead += stride;
+        v_after = idx_ahead < count ? __ldg(list + idx_ahead) : -1;
+        Row<LANES, 1> own;
+        if (valid) row_load(own, rc, v, gl);
+        Row<LANES, 1> acc;
+        row_zero(acc);
+        // the lane groups of a warp walk their nodes' batches in lockstep:
+        // the warp loops over the longest arc range among its groups
+        const int64_t len = valid ? end - beg : 0;
+        int64_t len_max = len;
+#pragma unroll
+        for (int o = LANES; o < 32; o <<= 1)
+            len_max = max(len_max, (int64_t)__shfl_xor_sync(kFull, (long long)len_max, o));
+        if (len_max > 0) {
+            int32_t t[TPL];
+            load_targets(t, beg, valid ? end : beg);
+            issue(t, 0);
+            load_targets(t, beg + UA, valid ? end : beg);
+            int st = 0;
+            for (int64_t k = 0; k < len_max; k += UA) {
+                if (k + UA < len_max) {
+                    issue(t, st ^ 1);
+                    load_targets(t, beg + k + 2 * UA, valid ? end : beg);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+#pragma unroll
+                for (int u = 0; u < UA; ++u)
+                    acc.v[0] = vmax4(acc.v[0], ring[(st * UA + u) * 32 + lane]);
+                st ^= 1;
+            }
+        }
+        (void)gmask;
+        if (valid && gl == 0) {
+            c_scan += (uint32_t)len;
+            c_gather += (uint32_t)len;
+        }
+        const bool any = len > 0;
+        const bool inR = valid && !first && test_bit(Fc, v);
+        const bool need = valid && (any || inR);
+        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write, &own);
+        warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
+    }
+    cp_async_wait<0>();
+    flush_counters(p, cur, mt, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
+}
+
 // Hub nodes: combine the segment partials written by k_union_warp, then
 // finish like any other node.  A lane group per hub.
 template <int LANES, int VPL>
@@ -2210,7 +2329,15 @@ struct UnionKernels {
         } else {
             k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
         }
-        k_union_small<LANES, VPL, false><<<sblocks, kBlock, 0, ss>>>(p);
+        bool small_done = false;
+        if constexpr (VPL == 1 && LANES <= 8) {
+            if (p.small_variant == 3) {
+                k_union_small_async<LANES>
+                    <<<sblocks, kBlock, SmallAsyncCfg<LANES>::smem_per_block, ss>>>(p);
+                small_done = true;
+            }
+        }
+        if (!small_done) k_union_small<LANES, VPL, false><<<sblocks, kBlock, 0, ss>>>(p);
         if constexpr (has_sparse_path<LANES, VPL>())
             k_union_small<LANES, VPL, true><<<sblocks, kBlock, 0, ss>>>(p);
         if (ss != s) {
@@ -2238,6 +2365,22 @@ struct UnionKernels {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_union_small<LANES, VPL, false>, kBlock, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_union_warp<LANES, VPL>, kBlock, 0);
         return a < b ? a : b;
+    }
+    // Resident blocks of the asynchronous-copy small-degree kernel (0 where
+    // it does not apply); also opts it in to more than 48 KB of shared memory.
+    static int small_async_occupancy()
+    {
+        if constexpr (VPL == 1 && LANES <= 8) {
+            const size_t smem = SmallAsyncCfg<LANES>::smem_per_block;
+            cudaFuncSetAttribute(k_union_small_async<LANES>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int nb = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_union_small_async<LANES>, kBlock,
+                                                          smem);
+            return nb;
+        } else {
+            return 0;
+        }
     }
     // Resident blocks of the asynchronous-copy warp kernel (0 where it does
     // not apply); also opts it in to more than 48 KB of shared memory.
@@ -2277,6 +2420,16 @@ cudaError_t with_width(int W, F &&f)
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+
+int small_async_blocks(int W)
+{
+    int nb = 0;
+    with_width(W, [&](auto k) {
+        nb = decltype(k)::small_async_occupancy();
+        return cudaSuccess;
+    });
+    return nb;
+}
 
 int union_async_warps(int W, int nsm)
 {

@@ -1,10 +1,11 @@
 // Autotuner: picks the launch parameters of the union pass for one graph by
 // timing them.  The tuned knobs are the degree split (small_max_deg: nodes
 // per lane group vs per warp; hub_min_deg: segment length of hub nodes), the
-// gather variant of the warp kernel and, as a second stage on the best of
-// those, whether late passes push (scatter) or pull (systolic).  Each candidate gets its own context
-// in the caller's workspace, one untimed warm-up run and one timed run of the
-// whole of Algorithm 2; the fastest wins.  Results are remembered in a text
+// gather variant (register batches, or asynchronous copies for the warp or
+// the small-degree kernel) and, as a second stage on the best of those,
+// whether late passes push (scatter) or pull (systolic).  Each candidate gets
+// its own context in the caller's workspace, one untimed warm-up run and one
+// timed run of the whole of Algorithm 2; the fastest wins.  Results are remembered in a text
 // cache (one "key value..." line per tuned shape) so that later calls with the
 // same GPU, row width and graph size skip the timing.
 #include <cuda_runtime.h>
@@ -132,11 +133,11 @@ extern "C" int hanf_autotune(int64_t n, int64_t arcs, const int64_t *offsets,
     };
     const int32_t smalls[] = {32, 128, 256, 1024, 4096};
     const int32_t hubs[] = {4096, 16384, 65536};
-    const int32_t variants[] = {1, 2};
+    const int32_t variants[] = {1, 2, 3};
     for (int32_t vsm : smalls)
         for (int32_t vh : hubs)
             for (int32_t gv : variants) {
-                if (gv == 2 && ((1 << log2m) * o.runs > 128 || o.layout)) continue;   // not applicable
+                if (gv >= 2 && ((1 << log2m) * o.runs > 128 || o.layout)) continue;   // not applicable
                 hanf_opts c = o;
                 c.small_max_deg = vsm;
                 c.hub_min_deg = vh;

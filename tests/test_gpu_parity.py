@@ -217,6 +217,15 @@ def test_async_gather_variant(H, oracle, log2m):
                   small_max_deg=4, hub_min_deg=256)
 
 
+@pytest.mark.parametrize("log2m", [4, 5, 6, 7])
+def test_small_async_variant(H, oracle, log2m):
+    """Asynchronous row copies in the small-degree kernel (gather_variant 3):
+    the same registers, T and N(t); frontier off makes every pass use it."""
+    for off, tgt in (G.rmat(13, seed=11), G.web(1 << 12, seed=6), G.empty(70)):
+        for frontier in ("off", "auto"):
+            check_run(H, oracle, off, tgt, log2m, frontier=frontier, gather_variant=3)
+
+
 def test_autotune_picks_a_candidate_and_caches_it(H, oracle, tmp_path):
     off, tgt = G.rmat(12, seed=13)
     cache = tmp_path / "tune.txt"
