@@ -92,3 +92,32 @@ def test_ed_interval_and_run_stats_match_oracle(H, oracle):
     for k in a:
         assert a[k][0] == pytest.approx(b[k][0], rel=1e-12)
         assert a[k][1] == pytest.approx(b[k][1], rel=1e-9, abs=1e-12)
+
+
+def test_structs_match_header(H, tmp_path):
+    """The binding's ctypes structures have the header's layout: a C program
+    compiled against include/hanf.h prints every field's offset and the
+    sizes, which must equal the ctypes ones."""
+    import ctypes
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hanf.h"', "int main(void) {"]
+    expect = []
+    for cname, ctype in (("hanf_opts", H.Opts), ("hanf_job", H.Job)):
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(ctypes.sizeof(ctype))
+        for field, _ in ctype._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {field}));')
+            expect.append(getattr(ctype, field).offset)
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == expect
