@@ -28,8 +28,10 @@
  * search, the closed-form neighbourhood functions (Section 4 counterexample;
  * paths, cycles, stars, complete digraphs), Theorem 1 / Vysochanskii-Petunin
  * bands over seeds, closed-form distance statistics, Algorithm 3 brackets of
- * exact effective diameters, and per-node eccentricity / distance-sum bounds
- * against breadth-first search.
+ * exact effective diameters, per-node eccentricity / distance-sum bounds
+ * against breadth-first search, per-node statistics of hand-worked E(0..T)
+ * sequences, the published FNV-1a-64 test vectors of the register digest, and
+ * the threaded per-node sizes summed to exactly ora_sum_sizes' value.
  *
  * Parity unpinned: the spid and effective-diameter values the paper measures
  * on its datasets (Table 2) -- the datasets are absent, so these statistics
@@ -179,6 +181,73 @@ ORA_API double ora_sum_sizes(const uint8_t *c, int64_t n, int32_t m)
         s = t;
     }
     return s + comp;
+}
+
+/* size(c[v]) of every node into out[0..n): the nodes are independent, so
+ * the loop may be split across threads without changing any value.  With
+ * ora_neumaier_sum below it gives exactly ora_sum_sizes' result (same
+ * values, same summation order). */
+ORA_API void ora_sizes(const uint8_t *c, int64_t n, int32_t m, double *out, int32_t threads)
+{
+    int64_t v;
+    (void)threads;
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+    for (v = 0; v < n; ++v)
+        out[v] = ora_size(c + v * m, m);
+}
+
+/* Neumaier-compensated sum of x[0..n), left to right. */
+ORA_API double ora_neumaier_sum(const double *x, int64_t n)
+{
+    double s = 0.0, comp = 0.0;
+    int64_t i;
+    for (i = 0; i < n; ++i) {
+        double t = s + x[i];
+        if (fabs(s) >= fabs(x[i])) comp += (s - t) + x[i];
+        else comp += (x[i] - t) + s;
+        s = t;
+    }
+    return s + comp;
+}
+
+/* ------------------------------------------------------------------ */
+/* Register digest (a check value for comparing whole counter arrays;  */
+/* not part of the method).                                            */
+/* ------------------------------------------------------------------ */
+
+/* FNV-1a, 64-bit (Fowler, Noll, Vo): start from the offset basis; for every
+ * byte, xor it into the hash, then multiply by the FNV prime 2^40 + 2^8 +
+ * 0xb3, modulo 2^64. */
+ORA_API uint64_t ora_fnv1a64(const uint8_t *p, int64_t len)
+{
+    uint64_t h = 14695981039346656037ULL;
+    int64_t i;
+    for (i = 0; i < len; ++i) {
+        h ^= (uint64_t)p[i];
+        h *= 1099511628211ULL;
+    }
+    return h;
+}
+
+/* Digest of the counters of nodes 0..n-1 (m registers each): for node v,
+ * FNV-1a-64 of the eight bytes of v (least significant first) followed by
+ * the m bytes of c[v]; the digest is the sum of these values modulo 2^64.
+ * Addition modulo 2^64 is associative, so the node loop may be split across
+ * threads. */
+ORA_API uint64_t ora_digest(const uint8_t *c, int64_t n, int32_t m, int32_t threads)
+{
+    uint64_t total = 0;
+    int64_t v;
+    (void)threads;
+#pragma omp parallel for schedule(static) reduction(+ : total) num_threads(threads > 0 ? threads : 1)
+    for (v = 0; v < n; ++v) {
+        uint8_t buf[8 + 256];
+        int32_t i;
+        for (i = 0; i < 8; ++i) buf[i] = (uint8_t)((uint64_t)v >> (8 * i));
+        memcpy(buf + 8, c + v * m, (size_t)m);
+        total += ora_fnv1a64(buf, 8 + (int64_t)m);
+    }
+    return total;
 }
 
 /* The whole of Algorithm 2 for one run: prints (stores) N(t) before each
@@ -385,13 +454,32 @@ ORA_API void ora_ed_interval(const double *N, int32_t T, double alpha, double ep
         if (N[t] / M >= alpha * (1.0 + 2.0 * eps)) { *hi = t; break; }
 }
 
-/* Per-node statistics of the estimates E_v(t) = size(c_t[v]), t = 0..T, of
+/* Statistics of one node's estimates E(0..T) = size(c_t[v]), t = 0..T, of
  * one run of Algorithm 2 (the radius distribution and closeness centrality
- * proposed in the paper's conclusion): reach = E_v(T); dist = sum over
- * t = 1..T of t (E_v(t) - E_v(t-1)); ecc = the last t with
- * E_v(t) != E_v(t-1) (0 if none); rad = the first t with
- * E_v(t) >= alpha E_v(T).  Keeps every E_v(t): for small graphs.  Returns T,
- * or -1 if cap passes were not enough, -2 on allocation failure. */
+ * proposed in the paper's conclusion): reach = E(T); dist = sum over
+ * t = 1..T of t (E(t) - E(t-1)); ecc = the last t with E(t) != E(t-1) (0 if
+ * none); rad = the first t with E(t) >= alpha E(T). */
+ORA_API void ora_seq_stats(const double *E, int32_t T, double alpha, double *reach,
+                           double *dist, int32_t *ecc, int32_t *rad)
+{
+    double s = 0.0, last = E[T];
+    int32_t t, e = 0, r = -1;
+    for (t = 0; t <= T; ++t) {
+        if (t > 0 && E[t] != E[t - 1]) {
+            s = s + (double)t * (E[t] - E[t - 1]);
+            e = t;
+        }
+        if (r < 0 && E[t] >= alpha * last) r = t;
+    }
+    *reach = last;
+    *dist = s;
+    *ecc = e;
+    *rad = r;
+}
+
+/* Per-node statistics (ora_seq_stats) of every node of one run of Algorithm
+ * 2.  Keeps every E_v(t): for small graphs.  Returns T, or -1 if cap passes
+ * were not enough, -2 on allocation failure. */
 ORA_API int32_t ora_node_stats(const int64_t *off, const int32_t *tgt, int64_t n, int32_t b,
                                uint64_t seed, double alpha, int32_t cap, double *reach,
                                double *dist, int32_t *ecc, int32_t *rad)
@@ -400,8 +488,9 @@ ORA_API int32_t ora_node_stats(const int64_t *off, const int32_t *tgt, int64_t n
     size_t bytes = (size_t)(n ? n : 1) * (size_t)m;
     uint8_t *c = (uint8_t *)malloc(bytes), *cn = (uint8_t *)malloc(bytes);
     double *E = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)(n ? n : 1));
+    double *seq = (double *)malloc(sizeof(double) * (size_t)cap);
     int64_t v;
-    if (!c || !cn || !E) { free(c); free(cn); free(E); return -2; }
+    if (!c || !cn || !E || !seq) { free(c); free(cn); free(E); free(seq); return -2; }
     ora_init(c, n, b, seed);
     for (t = 0; t < cap; ++t) {
         int64_t changed;
@@ -413,22 +502,10 @@ ORA_API int32_t ora_node_stats(const int64_t *off, const int32_t *tgt, int64_t n
     }
     if (T >= 0) {
         for (v = 0; v < n; ++v) {
-            double s = 0.0, last = E[(size_t)T * n + v];
-            int32_t e = 0, r = -1;
-            for (t = 0; t <= T; ++t) {
-                double Et = E[(size_t)t * n + v];
-                if (t > 0 && Et != E[(size_t)(t - 1) * n + v]) {
-                    s = s + (double)t * (Et - E[(size_t)(t - 1) * n + v]);
-                    e = t;
-                }
-                if (r < 0 && Et >= alpha * last) r = t;
-            }
-            reach[v] = last;
-            dist[v] = s;
-            ecc[v] = e;
-            rad[v] = r;
+            for (t = 0; t <= T; ++t) seq[t] = E[(size_t)t * n + v];
+            ora_seq_stats(seq, T, alpha, reach + v, dist + v, ecc + v, rad + v);
         }
     }
-    free(c); free(cn); free(E);
+    free(c); free(cn); free(E); free(seq);
     return T;
 }

@@ -92,6 +92,17 @@ def _load():
         lib.ora_node_stats.argtypes = [_i64p, _i32p, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_uint64, ctypes.c_double, ctypes.c_int32,
                                        _f64p, _f64p, _i32p, _i32p]
+        lib.ora_sizes.restype = None
+        lib.ora_sizes.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, _f64p, ctypes.c_int32]
+        lib.ora_neumaier_sum.restype = ctypes.c_double
+        lib.ora_neumaier_sum.argtypes = [_f64p, ctypes.c_int64]
+        lib.ora_fnv1a64.restype = ctypes.c_uint64
+        lib.ora_fnv1a64.argtypes = [_u8p, ctypes.c_int64]
+        lib.ora_digest.restype = ctypes.c_uint64
+        lib.ora_digest.argtypes = [_u8p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
+        lib.ora_seq_stats.restype = None
+        lib.ora_seq_stats.argtypes = [_f64p, ctypes.c_int32, ctypes.c_double, _f64p, _f64p,
+                                      _i32p, _i32p]
         lib.ora_stats.restype = None
         lib.ora_stats.argtypes = [_f64p, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                   _f64p]
@@ -171,6 +182,40 @@ def union_pass(offsets, targets, c: np.ndarray, threads: int = 1):
 def sum_sizes(c: np.ndarray) -> float:
     c = np.ascontiguousarray(c, dtype=np.uint8)
     return float(_load().ora_sum_sizes(_p(c, _u8p), c.shape[0], c.shape[1]))
+
+
+def sizes(c: np.ndarray, threads: int = 1) -> np.ndarray:
+    """size(c[v]) of every node (Algorithm 1), nodes split across threads."""
+    c = np.ascontiguousarray(c, dtype=np.uint8)
+    out = np.empty(max(c.shape[0], 1), dtype=np.float64)
+    _load().ora_sizes(_p(c, _u8p), c.shape[0], c.shape[1], _p(out, _f64p), threads)
+    return out[:c.shape[0]]
+
+
+def neumaier_sum(x) -> float:
+    """Neumaier-compensated sum, left to right."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(_load().ora_neumaier_sum(_p(x, _f64p), x.size))
+
+
+def sum_sizes_mt(c: np.ndarray, threads: int = 1) -> float:
+    """N = sum_v size(c[v]): the value ora_sum_sizes returns, with the
+    per-node sizes computed on several threads."""
+    return neumaier_sum(sizes(c, threads))
+
+
+def fnv1a64(data: bytes) -> int:
+    buf = np.frombuffer(bytes(data) or b"\0", dtype=np.uint8)
+    return int(_load().ora_fnv1a64(_p(buf, _u8p), len(data)))
+
+
+def digest(c: np.ndarray, threads: int = 1) -> int:
+    """Sum over nodes v (mod 2^64) of FNV-1a-64(v as 8 little-endian bytes,
+    then the m register bytes of c[v])."""
+    c = np.ascontiguousarray(c, dtype=np.uint8)
+    if c.shape[0] == 0:
+        return 0
+    return int(_load().ora_digest(_p(c, _u8p), c.shape[0], c.shape[1], threads))
 
 
 def hyperanf(offsets, targets, b: int, seed: int, cap: int = 4096, threads: int = 1,
@@ -254,6 +299,16 @@ def stats_runs(N_runs, alpha_: float = 0.9, exclude_zero: bool = False) -> dict:
         x = np.array([p[k] for p in per])
         out[k] = (float(x.mean()), float(x.std(ddof=1)) if len(x) > 1 else 0.0)
     return out
+
+
+def seq_stats(E, alpha_: float = 0.9) -> dict:
+    """Per-node statistics of one node's estimates E(0..T)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    reach, dist = ctypes.c_double(), ctypes.c_double()
+    ecc, rad = ctypes.c_int32(), ctypes.c_int32()
+    _load().ora_seq_stats(_p(E, _f64p), E.size - 1, alpha_, ctypes.byref(reach),
+                          ctypes.byref(dist), ctypes.byref(ecc), ctypes.byref(rad))
+    return {"reach": reach.value, "dist": dist.value, "ecc": ecc.value, "radius": rad.value}
 
 
 def node_stats(offsets, targets, b: int, seed: int, alpha_: float = 0.9, cap: int = 512) -> dict:

@@ -30,6 +30,16 @@ MUTANTS = {
     "ied_wrong_side": ("(alpha - prevH) / (H - prevH)", "(H - alpha) / (H - prevH)"),
     "hash_constant_typo": ("0xBF58476D1CE4E5B9ULL", "0xBF58476D1CE4E5B8ULL"),
     "hash_seed_added_not_xored": ("ora_splitmix64(v ^ seed)", "ora_splitmix64(v + seed)"),
+    "sizes_skip_node0": ("for (v = 0; v < n; ++v)\n        out[v] = ora_size(",
+                         "for (v = 1; v < n; ++v)\n        out[v] = ora_size("),
+    "neumaier_drops_branch": ("else comp += (x[i] - t) + s;", "else comp += 0.0;"),
+    "digest_drops_node_id": ("buf[i] = (uint8_t)((uint64_t)v >> (8 * i));", "buf[i] = 0;"),
+    "fnv_prime_typo": ("h *= 1099511628211ULL;", "h *= 1099511628213ULL;"),
+    "seq_radius_strict": ("if (r < 0 && E[t] >= alpha * last) r = t;",
+                          "if (r < 0 && E[t] > alpha * last) r = t;"),
+    "seq_ecc_previous_pass": ("            e = t;\n", "            e = t - 1;\n"),
+    "seq_dist_weight_off_by_one": ("s = s + (double)t * (E[t] - E[t - 1]);",
+                                   "s = s + (double)(t - 1) * (E[t] - E[t - 1]);"),
     "ball_radius_off_by_one": ("if (r >= 0 && dist[u] >= r) continue;", "if (r >= 0 && dist[u] > r) continue;"),
 }
 

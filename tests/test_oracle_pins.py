@@ -449,3 +449,72 @@ def test_node_distance_sums_estimate_the_exact_ones(oracle):
     rad = np.array([oracle.node_stats(*G.path(n), 8, oracle.run_seed(SEED, s))["radius"][0]
                     for s in range(20)])
     assert abs(np.median(rad) - (int(np.ceil(0.9 * n)) - 1)) <= 2
+
+
+# ---------------------------------------------------------------- check values and helpers
+
+
+def test_fnv1a64_published_vectors(oracle):
+    for text, out in _golden("fnv1a64.txt"):
+        assert oracle.fnv1a64(text.strip('"').encode()) == int(out, 16)
+
+
+def test_digest_definition_and_sensitivity(oracle):
+    """digest = sum over v of FNV-1a-64(8 little-endian bytes of v, then the
+    row), modulo 2^64; it sees any single register change and any swap of two
+    rows, and does not depend on the thread count."""
+    rng = np.random.default_rng(4)
+    for m in (16, 64, 256):
+        c = rng.integers(0, 32, (37, m)).astype(np.uint8)
+        want = sum(oracle.fnv1a64(v.to_bytes(8, "little") + c[v].tobytes())
+                   for v in range(c.shape[0])) % 2**64
+        assert oracle.digest(c, threads=1) == want
+        assert oracle.digest(c, threads=3) == want
+        for v, j in ((0, 0), (36, m - 1), (17, m // 2)):
+            d = c.copy()
+            d[v, j] ^= 1
+            assert oracle.digest(d) != want
+        d = c.copy()
+        d[[3, 4]] = d[[4, 3]]
+        assert not np.array_equal(d, c) and oracle.digest(d) != want
+    assert oracle.digest(np.zeros((0, 16), np.uint8)) == 0
+
+
+def test_parallel_sizes_equal_sum_sizes(oracle):
+    """The per-node sizes computed on several threads, summed by the
+    Neumaier loop, give exactly ora_sum_sizes' value."""
+    rng = np.random.default_rng(8)
+    for b in (4, 6, 8):
+        c = np.minimum(rng.geometric(0.5, (3001, 1 << b)) - 1, 31).astype(np.uint8)
+        c[::7] = 0                                  # empty counters: linear counting
+        x = oracle.sizes(c, threads=4)
+        assert x.shape == (3001,)
+        assert x[5] == oracle.size(c[5]) and x[0] == oracle.size(c[0]) and x[-1] == oracle.size(c[-1])
+        assert oracle.neumaier_sum(x) == oracle.sum_sizes(c)
+        assert oracle.sum_sizes_mt(c, threads=3) == oracle.sum_sizes(c)
+
+
+def test_neumaier_sum_is_compensated(oracle):
+    # plain left-to-right summation gives 0 and 1 here; the exact sums are 1 and 2
+    assert oracle.neumaier_sum([1e16, 1.0, -1e16]) == 1.0
+    assert oracle.neumaier_sum([1.0, 1e100, 1.0, -1e100]) == 2.0
+    x = np.random.default_rng(1).standard_normal(10000) * 1e6
+    assert oracle.neumaier_sum(x) == pytest.approx(math.fsum(x), rel=0, abs=1e-6)
+
+
+# (E(0..T), alpha) -> reach, distance sum, eccentricity, effective radius,
+# each worked out by hand from the definitions
+SEQUENCES = [
+    ([1.0, 3.0, 3.0, 7.0, 10.0], 0.9, 10.0, 1 * 2 + 3 * 4 + 4 * 3, 4, 4),
+    ([1.0, 5.0, 9.0, 9.0], 0.9, 9.0, 1 * 4 + 2 * 4, 2, 2),
+    ([2.0, 5.0, 10.0], 0.5, 10.0, 1 * 3 + 2 * 5, 2, 1),      # E(1) = alpha E(T) exactly
+    ([1.0], 0.9, 1.0, 0.0, 0, 0),
+    ([4.0, 4.0, 4.0], 0.9, 4.0, 0.0, 0, 0),
+    ([1.0, 2.0, 2.0, 2.0, 3.0, 3.0], 0.6, 3.0, 1 * 1 + 4 * 1, 4, 1),
+]
+
+
+@pytest.mark.parametrize("E,alpha_,reach,dist,ecc,rad", SEQUENCES)
+def test_per_node_statistics_of_hand_written_sequences(oracle, E, alpha_, reach, dist, ecc, rad):
+    got = oracle.seq_stats(E, alpha_)
+    assert got == {"reach": reach, "dist": dist, "ecc": ecc, "radius": rad}
