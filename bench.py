@@ -2,18 +2,20 @@
 """Throughput benchmark of HyperANF run to stabilisation on GB300.
 
 One step = the whole hot path on one batch: initialise every counter, then
-estimate N(t) and run union passes (frontier-skipping, systolic when few
-counters change) until a pass changes nothing, then the statistics.  The
-metric is arcs x registers merged per second: every pass of Algorithm 2
-merges each arc's m registers (R runs: R*m), so a step counts
-passes * arcs * m * R; passes whose merges the frontier proves redundant are
-counted, as Algorithm 2 performs them (the gathers actually issued are
-reported beside it).
+estimate N(t) and run union passes (frontier-skipping, systolic or pure push
+when few counters change) until a pass changes nothing.  The metric is
+arcs x registers merged per second of union-kernel time: every successor
+counter a pass actually gathers merges m registers per run, so a step counts
+(arcs gathered) * m * R, divided by the time of the union launches (measured
+with CUDA events in a profiled run of the same context options).  The nominal
+rate of Algorithm 2 (every arc merged in every pass, passes * arcs * m * R per
+step time) and the gathered merges per step time are reported beside it.
 
 Default workload: directed R-MAT scale 27 (134M nodes, edge factor 16,
-~2.1e9 arcs drawn, int64 offsets / int32 targets), m = 64 byte registers,
-one run.  Inputs (>= 10 GB of CSR and counters) are far larger than the 129 MB
-L2, so no flush is needed between steps.
+~2.1e9 arcs, int64 offsets / int32 targets), m = 64 byte registers, one run.
+The timed steps run the whole loop as one CUDA graph (the product's fastest
+driver).  Inputs (>= 10 GB of CSR and counters) are far larger than the
+129 MB L2, so no flush is needed between steps.
 
 With torchrun (N > 1) every rank runs an independent replica on its own GPU
 (the path needs no exchange): value = all ranks' merges / max rank time.
@@ -35,6 +37,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "arcs×registers merged/s per iteration"
+METRIC_DEFINITION = ("(successor counters gathered) x m x R per step / union-kernel time per "
+                     "step; nominal_rate = passes x arcs x m x R / step time")
 UNIT = "arcs*registers/s"
 
 WORKLOADS = {
@@ -146,23 +150,32 @@ def gpu_index_for(device):
 # ------------------------------------------------------------------ profile summary
 
 def ncu_traffic(workload, layout="byte"):
-    """Per-launch DRAM bytes of the union kernel from the committed ncu
-    summary of this workload and register layout, or None when there is none
-    or the kernel source changed since the capture."""
+    """Per-launch DRAM bytes of one pass's union launches from the committed
+    ncu record of this workload and register layout (profiles/traffic.json),
+    or None when there is none or the kernel source changed since the
+    capture."""
     import hashlib
-    suffix = "" if layout == "byte" else f"_{layout}"
-    path = os.path.join(ROOT, "profiles", f"union_{workload}{suffix}.md")
-    if not os.path.exists(path):
-        return None
-    text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h:
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[workload][layout]
+    except (OSError, KeyError, ValueError):
         return None
     src = open(os.path.join(ROOT, "paper_1011_5599_gb300", "csrc", "hanf_kernels.cu"), "rb").read()
-    if hashlib.sha256(src).hexdigest() != h.group(1):
+    if hashlib.sha256(src).hexdigest() != rec.get("kernel_source_sha256"):
         return None
-    return float(m.group(1))
+    return float(rec["traffic_bytes_per_launch"])
+
+
+def union_bytes(row, n, row_bytes):
+    """Algorithmic bytes of one pass's union launches from its trace row: 4
+    per scanned arc (target id), a row per gathered successor, own counter
+    read and counter written, the offsets of every node in a pull pass over
+    all nodes (8 n), and the changed-node bitmaps read and written (n / 4)."""
+    b = 4 * row["arcs_scanned"] + row_bytes * (row["arcs_gathered"] + row["own_reads"]
+                                               + row["writes"])
+    if int(row["mode"]) in (0, 2):
+        b += 8 * n
+    return b + n / 4
 
 
 def measured_peak():
@@ -429,7 +442,7 @@ def main():
     ap.add_argument("--arena-gb", type=int, default=64, help="served stream: HBM budget")
     ap.add_argument("--loads", type=float, nargs="+", default=[0.5, 0.8, 1.5],
                     help="served stream: arrival rate as a fraction of one-at-a-time capacity")
-    ap.add_argument("--driver", default="host", choices=["host", "graph"])
+    ap.add_argument("--driver", default="graph", choices=["host", "graph"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
@@ -442,16 +455,9 @@ def main():
                     help="register layout: one byte each, or five bit-planes")
     ap.add_argument("--autotune", action="store_true",
                     help="pick degree split and gather variant with hanf_autotune first")
-    ap.add_argument("--gather-ceiling", action="store_true",
-                    help="build and run the random 64-byte row gather probe, then exit")
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="runs of the profiled context that give the union-kernel time")
     args = ap.parse_args()
-    if args.gather_ceiling:
-        src = os.path.join(ROOT, "paper_1011_5599_gb300", "probe", "gather_ceiling.cu")
-        exe = os.path.join(ROOT, "paper_1011_5599_gb300", "_lib", "gather_ceiling")
-        os.makedirs(os.path.dirname(exe), exist_ok=True)
-        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
-                        src], check=True)
-        return subprocess.run([exe]).returncode
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":
@@ -505,14 +511,12 @@ def main():
     kw = dict(scatter_den=args.scatter_den)
     kw.update(tuned)          # the tuner's choices, where it made one
     h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
-                 use_graph=args.driver == "graph", profile=args.driver == "host", **kw)
+                 use_graph=args.driver == "graph", **kw)
     for _ in range(args.warmup):
         h.run()
 
-    merges = 0
+    nominal = 0
     gathered = 0
-    union_ms = 0.0
-    union_bytes = 0.0
     launches = 0
     passes_list, T_list = [], []
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -523,11 +527,8 @@ def main():
         for _ in range(args.steps):
             N, T = h.run()
             c = h.counters()
-            merges += c["passes"] * arcs * m * R
+            nominal += c["passes"] * arcs * m * R
             gathered += c["arcs_gathered"] * m * R
-            union_ms += c["union_ms"]
-            union_bytes += (4 * c["arcs_scanned"]
-                            + row_bytes * (c["arcs_gathered"] + c["own_reads"] + c["writes"]))
             launches += int(c["launches"])
             passes_list.append(int(c["passes"]))
             T_list.append(int(max(T)))
@@ -535,23 +536,45 @@ def main():
         torch.cuda.synchronize()
         barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
-    from paper_1011_5599_gb300.replicas import reduce_max_sum
-    elapsed_all, merges_all = reduce_max_sum(elapsed, merges, device=device)
-    value = merges_all / elapsed_all
-    if args.trace and args.driver == "host":
-        h.run()
-        for row in h.trace():
-            gbs = (4 * row["arcs_scanned"] + row_bytes * (row["arcs_gathered"] + row["own_reads"]
-                                                  + row["writes"])) / (row["union_ms"] * 1e6)
+    h.close()
+    del h
+
+    # ---- union-kernel time: the same options with per-pass CUDA events ----
+    hp = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
+                  profile=True, **kw)
+    hp.run()
+    prof_ms, prof_bytes, prof_gathered, rows = 0.0, 0.0, 0, []
+    for _ in range(max(args.profile_steps, 1)):
+        hp.run()
+        rows = hp.trace()
+        prof_ms += sum(r["union_ms"] for r in rows)
+        prof_bytes += sum(union_bytes(r, n, row_bytes) for r in rows)
+        prof_gathered += hp.counters()["arcs_gathered"] * m * R
+    psteps = max(args.profile_steps, 1)
+    if prof_gathered != psteps * gathered / args.steps:
+        raise RuntimeError("the profiled run gathered a different number of counters")
+    if args.trace:
+        for row in rows:
+            gbs = union_bytes(row, n, row_bytes) / (row["union_ms"] * 1e6)
             print(json.dumps({**row, "algorithmic_GBps": gbs}), file=sys.stderr)
+    union_s = prof_ms / 1e3 / psteps                  # union-kernel seconds per step
+    union_launch_ms = prof_ms / max(len(rows) * psteps, 1)
+    bytes_per_launch = prof_bytes / max(len(rows) * psteps, 1)
+    hp.close()
+    del hp
+
+    from paper_1011_5599_gb300.replicas import reduce_max_sum
+    step_s = elapsed / args.steps
+    step_all, gathered_all = reduce_max_sum(step_s, gathered / args.steps, device=device)
+    union_all, _ = reduce_max_sum(union_s, 0.0, device=device)
+    _, nominal_all = reduce_max_sum(0.0, nominal / args.steps, device=device)
+    value = gathered_all / union_all
     stat = {}
     try:
         from paper_1011_5599_gb300.hanf import stats
         stat = stats(N[0])
     except Exception:
         pass
-    h.close()
-    del h
 
     # ---- end to end through the C ABI with host buffers (pinned) ----
     e2e = None
@@ -562,7 +585,7 @@ def main():
         tgt_h.copy_(tgt)
         del off, tgt
         torch.cuda.empty_cache()
-        e_merges, d2h = 0, 0
+        e_merges, d2h = 0, 0     # merges counted as for value: counters gathered
         # one untimed warm-up so the workspace is in torch's cache
         HyperANF(off_h, tgt_h, log2m, 0x5EED, runs=R, frontier="auto", device=device).close()
         barrier()
@@ -572,7 +595,7 @@ def main():
             with HyperANF(off_h, tgt_h, log2m, 0x5EED, runs=R, frontier="auto",
                           device=device, use_graph=args.driver == "graph") as he:
                 Ne, Te = he.run()
-                e_merges += he.counters()["passes"] * arcs * m * R
+                e_merges += he.counters()["arcs_gathered"] * m * R
                 d2h += sum(x.nbytes for x in Ne)
         torch.cuda.synchronize()
         e_el = time.perf_counter() - t0
@@ -591,18 +614,22 @@ def main():
                "sample": f"{desc}; {secs:.1f} s"}
 
     peak, peak_kind = measured_peak()
-    steps_passes = sum(passes_list)
-    achieved = union_bytes / (union_ms / 1e3) / 1e9 if union_ms > 0 else None
+    achieved = bytes_per_launch / (union_launch_ms / 1e3) / 1e9 if union_launch_ms > 0 else None
     traffic = ncu_traffic(args.workload, args.layout)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic, "peak_kind": peak_kind, "kernel": "union launches of one pass (k_union_*, k_scatter*, k_hub_finish)",
-            "algorithmic_bytes_per_launch": union_bytes / max(steps_passes, 1),
-            "avg_launch_ms": union_ms / max(steps_passes, 1)}
+            "traffic": traffic, "peak_kind": peak_kind,
+            "kernel": "union launches of one pass (k_union_*, k_scatter*, k_hub_finish)",
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": union_launch_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * elapsed_all / args.steps, "higher_is_better": True,
+            "ms_per_step": 1e3 * step_all, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "metric_definition": METRIC_DEFINITION,
+            "union_ms_per_step": 1e3 * union_all,
+            "nominal_rate": nominal_all / step_all,
+            "gathered_per_step_time": gathered_all / step_all,
             "config": {"workload": wl["text"], "n": n, "arcs": arcs, "m": m, "runs": R,
                        "layout": args.layout, "frontier": "auto", "driver": args.driver,
                        "scatter_den": args.scatter_den or "default",
@@ -610,7 +637,6 @@ def main():
                        "l2": "inputs larger than L2 (no flush)", "tuned": tuned,
                        "graph_gen_s": round(t_gen, 2)},
             "T": T_list[-1], "passes_per_step": passes_list[-1],
-            "gathered_rate": gathered / elapsed if elapsed else None,
             "stats": {k: float(v) for k, v in stat.items()},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks.summary()}

@@ -168,6 +168,20 @@ HANF_API int hanf_run(hanf_ctx *ctx, int32_t max_iter, double *N_out, int32_t ca
  * count * m bytes, node-major.  Synchronises the stream. */
 HANF_API int hanf_registers(hanf_ctx *ctx, int32_t run, int64_t first, int64_t count, uint8_t *out);
 
+/* Digest of the registers of run r for nodes [first, first+count) (input
+ * ids): the sum modulo 2^64, over those nodes v, of FNV-1a-64 (Fowler, Noll,
+ * Vo; 64-bit offset basis and prime) of the eight little-endian bytes of
+ * v - first followed by the m registers of c[v], one byte each, whatever the
+ * storage layout.  A check value for Algorithm 2's state (the counters
+ * c_t of Section 3.2): two arrays with the same registers give the same
+ * digest, and any difference changes it except with probability about
+ * 2^-64, so a run can be compared after every pass with another
+ * implementation without copying n*m bytes out.  *digest_out (host).  Uses
+ * the context's control block as its only scratch.  Synchronises the
+ * stream. */
+HANF_API int hanf_digest(hanf_ctx *ctx, int32_t run, int64_t first, int64_t count,
+                         uint64_t *digest_out);
+
 /* Current pass index t (number of passes run since initialisation). */
 HANF_API int hanf_current_t(hanf_ctx *ctx, int32_t *t_out);
 
@@ -203,17 +217,21 @@ HANF_API int hanf_stats(const double *N, int32_t T, double alpha, int32_t exclud
  * serving loop whose device memory was all reserved up front, or a process
  * sharing the GPU with an allocator that owns all of it, where cudaMalloc
  * would fail or synchronise the device).
- *   regs: device pointer to n rows of runs * 2^log2m bytes (row v holds run 0's
- *     registers, then run 1's, ...; values 0..31), the layout this library keeps.
- *   N_out: device pointer to `runs` doubles, N for each run.
+ *   regs: device pointer, 16-byte aligned, to n rows of runs * 2^log2m bytes
+ *     (row v holds run 0's registers, then run 1's, ...; values 0..31), the
+ *     layout this library keeps.  A register above 31 makes its run's N NaN.
+ *   N_out: device pointer, 8-byte aligned, to `runs` doubles, N for each run.
  *   stream: cudaStream_t (NULL = default stream); the call only enqueues work.
  * Its scratch is one fixed array of 2^20 doubles (8 MiB) inside the library,
  * kept by every GPU that loads it until the process exits; runs * (ceil(n/64)
- * + ceil(n/262144)) must not exceed 2^20, otherwise it returns HANF_EINVAL.
- * The first call on each device looks the array's address up (once, with that
- * device current), so make it before any stream capture.  Calls share the
- * array and each overwrites what it reads; calls that overlap on the GPU race
- * and must be serialised by the caller. */
+ * + ceil(n/262144)) must not exceed 2^20, otherwise it returns HANF_EINVAL
+ * (as it does for a misaligned pointer), before enqueuing anything.
+ * The first call in each CUDA context (normally: on each device) looks the
+ * array's address up with that context current and remembers it by the
+ * context's id, so make that first call before any stream capture; a context
+ * created later (after cudaDeviceReset, or another driver-API context) gets
+ * its own lookup.  Calls share the array and each overwrites what it reads;
+ * calls that overlap on the GPU race and must be serialised by the caller. */
 HANF_API int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2m, int32_t runs,
                                   double *N_out, void *stream);
 

@@ -150,6 +150,9 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     s->ntiles = hanf::classify_blocks(n);
     s->max_hub = arcs / (s->d_hub + 1) + 1;
     s->max_seg = 2 * (arcs / s->d_hub) + 2;
+    if (s->max_seg >= (int64_t(1) << 31))   // hub segments are numbered with int32
+        return fail(HANF_EINVAL, "hub_min_deg=%d is too small for %lld arcs", s->d_hub,
+                    (long long)arcs);
     int64_t biggest = std::max<int64_t>({n + 1, 3 * s->ntiles + 1, s->max_hub + 1,
                                          hanf::relabel_count_elems(n)});
     s->scan_elems = hanf::scan_tmp_elems(biggest) * 2 + 64;
@@ -820,6 +823,22 @@ int hanf_registers(hanf_ctx *c, int32_t run, int64_t first, int64_t count, uint8
                              cudaMemcpyDeviceToHost, c->stream));
         CU(cudaStreamSynchronize(c->stream));
     }
+    return HANF_OK;
+}
+
+int hanf_digest(hanf_ctx *c, int32_t run, int64_t first, int64_t count, uint64_t *digest_out)
+{
+    if (!c || !digest_out) return fail(HANF_EINVAL, "NULL argument");
+    if (run < 0 || run >= c->plan.R) return fail(HANF_EINVAL, "run %d out of range", run);
+    if (first < 0 || count < 0 || first + count > c->plan.n)
+        return fail(HANF_EINVAL, "node range out of bounds");
+    unsigned long long *d = &c->plan.ctl->digest;
+    CU(cudaMemsetAsync(d, 0, sizeof *d, c->stream));
+    CU(hanf::launch_digest(c->plan, run, first, count, c->perm, d, c->stream));
+    unsigned long long h = 0;
+    CU(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    *digest_out = h;
     return HANF_OK;
 }
 

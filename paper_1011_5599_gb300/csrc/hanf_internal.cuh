@@ -34,6 +34,7 @@ struct DevCtl {
     unsigned long long changed_in_arcs;      // in-degree sum of the nodes the last pass changed
     // work counters since initialisation
     unsigned long long passes, push_passes, arcs_scanned, arcs_gathered, own_reads, writes;
+    unsigned long long digest;               // result of the last hanf_digest
 };
 
 // Everything a kernel needs that does not change between passes.  Passed by
@@ -143,6 +144,8 @@ cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *perm, int64_t
                                int64_t count, int W, uint8_t *out, cudaStream_t s);
 cudaError_t launch_gather_node_values(const void *src, const int32_t *perm, int64_t first,
                                       int64_t count, int elem_bytes, void *out, cudaStream_t s);
+cudaError_t launch_digest(const Plan &p, int32_t run, int64_t first, int64_t count,
+                          const int32_t *perm, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_unpack_rows(const uint8_t *regs, const int32_t *perm, int64_t first,
                                int64_t count, int m, uint8_t *out, cudaStream_t s);
 

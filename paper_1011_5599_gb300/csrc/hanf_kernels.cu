@@ -2272,6 +2272,59 @@ __global__ void k_punpack(const uint8_t *regs, const int32_t *perm, int64_t firs
     }
 }
 
+// Register digest (hanf_digest): for input ids first+i, i < count, FNV-1a-64
+// (offset basis 14695981039346656037, prime 2^40 + 2^8 + 0xb3) of the eight
+// little-endian bytes of i followed by the m registers of run r, one byte
+// each; the values are summed modulo 2^64, which makes the result
+// independent of the order the threads add them in.  A thread per node.
+__global__ void __launch_bounds__(kBlock) k_digest(Plan p, int32_t r, int64_t first,
+                                                   int64_t count, const int32_t *perm,
+                                                   unsigned long long *out)
+{
+    constexpr unsigned long long kBasis = 14695981039346656037ull;
+    constexpr unsigned long long kPrime = 1099511628211ull;
+    const uint8_t *regs = p.regs[p.ctl->parity];
+    unsigned long long acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = perm ? (int64_t)__ldg(perm + first + i) : first + i;
+        unsigned long long h = kBasis;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            h ^= ((unsigned long long)i >> (8 * k)) & 0xffull;
+            h *= kPrime;
+        }
+        if (p.layout == 0) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(regs + row * p.W + (int64_t)r * p.m);
+            for (int k = 0; k < (p.m >> 4); ++k) {
+                const uint4 x = q[k];
+                const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    h ^= (w4[j >> 2] >> (8 * (j & 3))) & 0xffu;
+                    h *= kPrime;
+                }
+            }
+        } else {
+            // five bit-planes of m bits: register j is bit j%32 of word j/32
+            // of every plane
+            const int P = p.m >> 5;
+            const uint32_t *q = reinterpret_cast<const uint32_t *>(regs + row * p.W);
+            for (int j = 0; j < p.m; ++j) {
+                uint32_t val = 0;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) val |= ((q[b * P + (j >> 5)] >> (j & 31)) & 1u) << b;
+                h ^= val;
+                h *= kPrime;
+            }
+        }
+        acc += h;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
 template <typename F>
 cudaError_t with_planes(int m, F &&f)
 {
@@ -2696,6 +2749,14 @@ cudaError_t launch_gather_node_values(const void *src, const int32_t *perm, int6
     else
         k_gather_vals<uint32_t><<<grid_for(count, kBlock), kBlock, 0, s>>>(
             static_cast<const uint32_t *>(src), perm, first, count, static_cast<uint32_t *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_digest(const Plan &p, int32_t run, int64_t first, int64_t count,
+                          const int32_t *perm, unsigned long long *out, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_digest<<<grid_for(count, kBlock), kBlock, 0, s>>>(p, run, first, count, perm, out);
     return cudaGetLastError();
 }
 

@@ -11,14 +11,17 @@
 // The scratch is one file-scope device array of kStaticScratchDoubles
 // doubles (8 MiB).  Every GPU that loads the library keeps its own copy until
 // the process exits.  Host code may not use the array's name as a device
-// address (on the host it is only a stand-in), so the first call on each
-// device looks the address up with cudaGetSymbolAddress while that device is
-// current and remembers it; make that first call before any stream capture.
-// All calls on a device share the array and it keeps the previous call's
-// contents: each call writes every partial before reading it, so nothing has
-// to be cleared, but calls that overlap on the GPU (on different streams, or
-// from different host threads) race on it and must be serialised by the
-// caller.
+// address (on the host it is only a stand-in), so the first call in each CUDA
+// context (normally: on each device) looks the address up with
+// cudaGetSymbolAddress while that context is current and remembers it under
+// the context's process-unique id; make that first call before any stream
+// capture.  Keying by context id keeps the address right for a context
+// created after cudaDeviceReset and for driver-API contexts other than the
+// primary one.  All calls in a context share the array and it keeps the
+// previous call's contents: each call writes every partial before reading
+// it, so nothing has to be cleared, but calls that overlap on the GPU (on
+// different streams, or from different host threads) race on it and must be
+// serialised by the caller.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,7 +38,7 @@ namespace {
 constexpr int64_t kStaticScratchDoubles = int64_t(1) << 20;   // 8 MiB
 constexpr int kThreads = 256;
 constexpr int kChunk = 4096;      // block partials summed by one first-level CTA
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
 
 static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
 
@@ -43,8 +46,17 @@ struct LcTable {
     double v[257];   // m ln(m / V) for V = 0..m (entry 0 unused)
 };
 
+// The scratch's device address per CUDA context, keyed by the context's id
+// (unique for the life of the process).  Driver entry points are looked up
+// through the runtime, so the library does not link the driver library.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
 std::mutex g_setup_mutex;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+unsigned long long g_ctx_ids[kMaxContexts];
+double *g_scratch_ptr[kMaxContexts];
+int g_contexts = 0;
 
 // the message is read back with hanf_last_error()
 int static_fail(int code, const std::string &msg)
@@ -56,23 +68,28 @@ int static_fail(int code, const std::string &msg)
 // size() of run r of node v: alpha_m m^2 / sum_j 2^-M[j] with the sum taken
 // exactly as an integer of 2^(31-M[j]) terms, and linear counting m ln(m/V)
 // when that estimate is at most 5m/2 and V registers are empty.
+// A register above 31 is outside the layout: the node's size is NaN, which
+// makes the run's N NaN.
 __device__ double static_node_size(const uint8_t *regs, int64_t v, int r, int m, int64_t W,
                                    double amm, const LcTable &lc)
 {
     const uint4 *q = reinterpret_cast<const uint4 *>(regs + v * W + (int64_t)r * m);
     unsigned long long S = 0;
     int V = 0;
+    bool bad = false;
     for (int k = 0; k < (m >> 4); ++k) {
         const uint4 x = q[k];
         const uint32_t w4[4] = {x.x, x.y, x.z, x.w};
         for (int j = 0; j < 4; ++j) {
             for (int s = 0; s < 32; s += 8) {
                 const uint32_t M = (w4[j] >> s) & 0xffu;
-                S += 1ull << (31 - M);
+                bad |= M > 31u;
+                S += M <= 31u ? 1ull << (31 - M) : 0ull;
                 V += M == 0;
             }
         }
     }
+    if (bad) return __longlong_as_double(0x7ff8000000000000ll);   // quiet NaN
     const double Z = 1.0 / ((double)S * 0x1p-31);
     double E = amm * Z;
     if (E <= 2.5 * (double)m && V > 0) E = lc.v[V];
@@ -138,6 +155,11 @@ extern "C" int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2
     if (runs < 1 || runs > 8) return static_fail(HANF_EINVAL, "runs outside 1..8");
     if (n < 0 || n >= (int64_t(1) << 31)) return static_fail(HANF_EINVAL, "n out of range");
     if (!N_out || (n > 0 && !regs)) return static_fail(HANF_EINVAL, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(regs) & 15)
+        return static_fail(HANF_EINVAL, "hanf_estimate_static: regs must be 16-byte aligned "
+                                        "(rows are read as 16-byte vectors)");
+    if (reinterpret_cast<uintptr_t>(N_out) & 7)
+        return static_fail(HANF_EINVAL, "hanf_estimate_static: N_out must be 8-byte aligned");
     const int m = 1 << log2m;
     const int64_t nblk = std::max<int64_t>(1, (n + 63) / 64);
     const int64_t nred = (nblk + kChunk - 1) / kChunk;
@@ -150,23 +172,54 @@ extern "C" int hanf_estimate_static(const uint8_t *regs, int64_t n, int32_t log2
                  runs, (long long)n, (long long)need, (long long)kStaticScratchDoubles);
         return static_fail(HANF_EINVAL, buf);
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return static_fail(HANF_ECUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return static_fail(HANF_ECUDA, "device index too large");
-    double *scratch;
+    cudaError_t e;
+    double *scratch = nullptr;
     {
-        // once per device, with that device current: the scratch's address
+        // once per context, with that context current: the scratch's address
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
-            void *ptr = nullptr;
+        if (!g_ctx_get_current || !g_ctx_get_id) {
+            cudaDriverEntryPointQueryResult q1, q2;
+            void *f1 = nullptr, *f2 = nullptr;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                                 &q1) != cudaSuccess ||
+                cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault,
+                                                 &q2) != cudaSuccess ||
+                q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+                return static_fail(HANF_ECUDA, "hanf_estimate_static: the driver's context "
+                                               "queries are unavailable");
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+        void *ptr = nullptr;
+        void *ctx = nullptr;
+        if (g_ctx_get_current(&ctx) != 0 || !ctx) {
+            // no context current on this thread yet: the symbol lookup makes
+            // the runtime's primary context current
             e = cudaGetSymbolAddress(&ptr, g_static_scratch);
             if (e != cudaSuccess)
                 return static_fail(HANF_ECUDA, std::string("cudaGetSymbolAddress failed: ") +
                                                    cudaGetErrorString(e));
-            g_scratch_ptr[dev] = static_cast<double *>(ptr);
+            if (g_ctx_get_current(&ctx) != 0 || !ctx)
+                return static_fail(HANF_ECUDA, "hanf_estimate_static: no current CUDA context");
         }
-        scratch = g_scratch_ptr[dev];
+        unsigned long long id = 0;
+        if (g_ctx_get_id(ctx, &id) != 0)
+            return static_fail(HANF_ECUDA, "hanf_estimate_static: cuCtxGetId failed");
+        for (int i = 0; i < g_contexts; ++i)
+            if (g_ctx_ids[i] == id) scratch = g_scratch_ptr[i];
+        if (!scratch) {
+            if (!ptr) {
+                e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+                if (e != cudaSuccess)
+                    return static_fail(HANF_ECUDA, std::string("cudaGetSymbolAddress failed: ") +
+                                                       cudaGetErrorString(e));
+            }
+            scratch = static_cast<double *>(ptr);
+            // a full table forgets its oldest entry
+            const int slot = g_contexts < kMaxContexts ? g_contexts++ : (int)(id % kMaxContexts);
+            g_ctx_ids[slot] = id;
+            g_scratch_ptr[slot] = scratch;
+        }
     }
     LcTable lc;
     for (int V = 0; V <= 256; ++V)

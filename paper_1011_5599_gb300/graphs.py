@@ -20,6 +20,8 @@ and 2), which are not available here and are stood in for by these recipes:
                optional symmetrisation; runs on any torch device (the CUDA
                random stream differs from the CPU one, so a graph is named by
                its recipe, seed and device);
+* ``rmat_multigraph`` R-MAT keeping every drawn arc (duplicates and loops),
+               for inputs past 2^31 arcs;
 * fixtures with closed-form neighbourhood functions: path, cycle, star,
   complete digraph, two cliques joined by a one-way path (Section 4), and a
   4-neighbour grid.
@@ -252,6 +254,65 @@ def rmat(scale: int, edge_factor: int = 16, seed: int = 1, a: float = 0.57, b: f
     del keys
     if as_numpy:
         return off.cpu().numpy(), tgt.cpu().numpy()
+    return off, tgt
+
+
+def rmat_multigraph(scale: int, edge_factor: int, seed: int = 1, a: float = 0.57,
+                    b: float = 0.19, c: float = 0.19, device: str = "cuda",
+                    buckets: int = 16, chunk: int = 1 << 26):
+    """R-MAT with every drawn arc kept: duplicate arcs and self-loops stay
+    (both are legal inputs, max being idempotent), so the arc count is exactly
+    edge_factor * 2^scale and can exceed 2^31.  Labels are scrambled as in
+    ``rmat``.  Arcs are binned by the top bits of their source and each bin is
+    sorted on its own, so no single sort or count sees 2^31 elements.
+    Returns (offsets int64, targets int32) as tensors on ``device``."""
+    import torch
+
+    n = 1 << scale
+    total = edge_factor * n
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    perm = torch.randperm(n, generator=g, device=device)
+    shift = max(scale - max(buckets.bit_length() - 1, 0), 0)
+    nb = n >> shift
+    bins = [[] for _ in range(nb)]
+    for s in range(0, total, chunk):
+        k = min(chunk, total - s)
+        src = torch.zeros(k, dtype=torch.int64, device=device)
+        dst = torch.zeros(k, dtype=torch.int64, device=device)
+        for _ in range(scale):
+            uu = torch.rand(k, generator=g, device=device)
+            sb = uu >= (a + b)
+            db = ((uu >= a) & (uu < a + b)) | (uu >= (a + b + c))
+            src = src * 2 + sb.to(torch.int64)
+            dst = dst * 2 + db.to(torch.int64)
+            del uu, sb, db
+        src = perm[src]
+        dst = perm[dst]
+        keys = (src << scale) | dst
+        bucket = src >> shift
+        order = torch.argsort(bucket, stable=True)
+        keys, bucket = keys[order], bucket[order]
+        cnt = torch.bincount(bucket, minlength=nb).tolist()
+        for i, piece in enumerate(torch.split(keys, cnt)):
+            if piece.numel():
+                bins[i].append(piece.clone())
+        del src, dst, keys, bucket, order
+    counts = torch.zeros(n, dtype=torch.int64, device=device)
+    tgt = torch.empty(total, dtype=torch.int32, device=device)
+    at = 0
+    for i in range(nb):
+        if not bins[i]:
+            continue
+        keys = torch.sort(torch.cat(bins[i])).values
+        bins[i] = None
+        counts += torch.bincount(keys >> scale, minlength=n)
+        tgt[at:at + keys.numel()] = (keys & (n - 1)).to(torch.int32)
+        at += keys.numel()
+        del keys
+    assert at == total
+    off = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    torch.cumsum(counts, 0, out=off[1:])
     return off, tgt
 
 

@@ -22,7 +22,8 @@ FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 
 # Every function declared in include/hanf.h.
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
-           "hanf_iterate", "hanf_run", "hanf_registers", "hanf_current_t", "hanf_counters",
+           "hanf_iterate", "hanf_run", "hanf_registers", "hanf_digest", "hanf_current_t",
+           "hanf_counters",
            "hanf_trace", "hanf_checkpoint_size", "hanf_checkpoint_save", "hanf_checkpoint_load",
            "hanf_continue", "hanf_node_stats", "hanf_node_radius", "hanf_stats",
            "hanf_ed_interval", "hanf_stats_runs",
@@ -98,6 +99,8 @@ def lib():
         L.hanf_run.argtypes = [_vp, _i32, ctypes.POINTER(_f64), _i32, ctypes.POINTER(_i32)]
         L.hanf_registers.restype = _i32
         L.hanf_registers.argtypes = [_vp, _i32, _i64, _i64, _vp]
+        L.hanf_digest.restype = _i32
+        L.hanf_digest.argtypes = [_vp, _i32, _i64, _i64, ctypes.POINTER(_u64)]
         L.hanf_current_t.restype = _i32
         L.hanf_current_t.argtypes = [_vp, ctypes.POINTER(_i32)]
         L.hanf_counters.restype = _i32
@@ -409,6 +412,14 @@ class HyperANF:
         out = np.zeros((max(count, 1), self.m), dtype=np.uint8)
         check(lib().hanf_registers(self._ctx, run, first, count, out.ctypes.data))
         return out[:count]
+
+    def digest(self, run: int = 0, first: int = 0, count: int | None = None) -> int:
+        """hanf_digest: check value of run r's registers of input ids
+        first..first+count-1 (ids counted from ``first``)."""
+        count = self.n - first if count is None else count
+        out = _u64()
+        check(lib().hanf_digest(self._ctx, run, first, count, ctypes.byref(out)))
+        return out.value
 
     @property
     def t(self) -> int:

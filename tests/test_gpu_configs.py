@@ -2,13 +2,15 @@
 
 * web-like graph, n = 2^20, m = 64, R = 8 runs batched: the oracle runs all
   eight runs completely; registers, T and N(t) are compared in full.
-* symmetrised R-MAT scale 24 (~5e8 arcs), m = 128: N(0) in full, and N(T)
-  exactly from connected components (on a symmetric graph the stabilised
-  counter of v is the union over v's component), plus sampled final
-  registers.
-* directed R-MAT scale 27 (~2.1e9 arcs), m = 64, in the launch configuration
-  the benchmark times: N(0) in full, registers of sampled nodes after 1 and 2
-  passes against breadth-first balls, and at stabilisation for sampled nodes.
+* symmetrised R-MAT scale 24 (~5e8 arcs), m = 128, and directed R-MAT scale
+  27 (~2.1e9 arcs), m = 64, in the launch configuration the benchmark times:
+  after every pass t the digest of all n counters (hanf_digest against the
+  oracle's digest of its own Jacobi pass), N(t), and the number of changed
+  counters are compared, then the whole run through the CUDA-graph driver.
+* an R-MAT multigraph of 2^25 nodes and 65 * 2^25 = 2,181,038,080 arcs (past
+  2^31; duplicate arcs and self-loops kept), m = 16: the same comparison after
+  every pass, for the default pass flavours, with pure-push passes off
+  (systolic instead), and with the frontier off (dense passes only).
 The large graphs are generated on the GPU and copied to the host for the
 oracle; nothing the oracle uses comes from the CUDA path's results.
 """
@@ -57,62 +59,99 @@ def test_web_2p20_eight_runs_full(H, oracle):
         np.testing.assert_allclose(N[r], No, rtol=RTOL, atol=0)
 
 
-def test_symmetric_rmat24_m128(H, oracle):
+def oracle_trajectory(oracle, off, tgt, log2m, seed, threads=THREADS):
+    """Algorithm 2 on the oracle, pass by pass: for t = 0..T the tuple
+    (N(t), digest of c_t, counters changed by pass t)."""
+    c = oracle.init(off.size - 1, log2m, seed)
+    traj = []
+    while True:
+        N = oracle.sum_sizes_mt(c, threads)
+        D = oracle.digest(c, threads)
+        c, changed = oracle.union_pass(off, tgt, c, threads)
+        traj.append((N, D, changed))
+        if changed == 0:
+            return traj
+        assert len(traj) < 200
+
+
+def check_every_pass(h, traj):
+    """Step the context with the host-loop driver and compare each t with the
+    oracle's trajectory; returns the pass modes of the trace (profile=True)."""
+    for t, (N, D, changed) in enumerate(traj):
+        assert h.t == t
+        assert h.digest(0) == D, f"t={t}: registers differ"
+        np.testing.assert_allclose(h.estimate()[0], N, rtol=RTOL, atol=0, err_msg=f"t={t}")
+        assert h.iterate() == changed, f"t={t}: changed counters"
+    assert h.iterate() == 0
+    return [int(row["mode"]) for row in h.trace()]
+
+
+def check_graph_driver(h, traj):
+    """hanf_run through the CUDA graph: same T, N(0..T) and final registers."""
+    N, T = h.run()
+    assert T[0] == len(traj) - 1
+    np.testing.assert_allclose(N[0], [x[0] for x in traj], rtol=RTOL, atol=0)
+    assert h.digest(0) == traj[-1][1]
+
+
+def test_symmetric_rmat24_m128_every_pass(H, oracle):
     import torch
     from paper_1011_5599_gb300 import graphs as G
     off_d, tgt_d = G.rmat(24, symmetrise=True, seed=1, device="cuda", as_numpy=False)
+    off, tgt = off_d.cpu().numpy(), tgt_d.cpu().numpy()
     log2m = 7
-    with H.HyperANF(off_d, tgt_d, log2m, SEED) as h:
-        N, T = h.run()
-        off, tgt = off_d.cpu().numpy(), tgt_d.cpu().numpy()
-        seed0 = oracle.run_seed(SEED, 0)
-        rng = np.random.default_rng(5)
-        deg = np.diff(off)
-        sample = list(rng.choice(np.nonzero(deg > 0)[0], 2)) + [int(np.argmax(deg))]
-        for v in sample:
-            got = h.registers(0, int(v), 1)[0]
-            assert np.array_equal(got, oracle.ball_registers(off, tgt, int(v), -1, log2m, seed0))
+    traj = oracle_trajectory(oracle, off, tgt, log2m, oracle.run_seed(SEED, 0))
+    assert len(traj) >= 4
+    with H.HyperANF(off_d, tgt_d, log2m, SEED, frontier="auto", use_graph=True,
+                    profile=True) as h:
+        check_every_pass(h, traj)
+        check_graph_driver(h, traj)
     del off_d, tgt_d
     torch.cuda.empty_cache()
-    n = off.size - 1
-    c0 = oracle.init(n, log2m, seed0)
-    np.testing.assert_allclose(N[0][0], oracle.sum_sizes(c0), rtol=RTOL)
-    del c0
-    np.testing.assert_allclose(N[0][-1], oracle.symmetric_final_sum(off, tgt, log2m, seed0),
-                               rtol=RTOL)
-    assert np.all(np.diff(N[0]) >= 0)
 
 
-def test_rmat27_benchmark_configuration(H, oracle):
-    """Scale 27 in the launch configuration the benchmark times (frontier
-    auto, host-loop driver with per-pass events)."""
+def test_rmat27_benchmark_configuration_every_pass(H, oracle):
+    """Scale 27, m = 64, frontier auto: the benchmark's graph (seed 1) and
+    options; every pass against the oracle, then the CUDA-graph driver the
+    benchmark times."""
     import torch
-    if host_ram_gb() < 40:
-        pytest.skip("needs ~40 GB of free host memory for the oracle checks")
+    if host_ram_gb() < 48:
+        pytest.skip("needs ~48 GB of free host memory for the oracle")
     from paper_1011_5599_gb300 import graphs as G
     off_d, tgt_d = G.rmat(27, seed=1, device="cuda", as_numpy=False)
-    log2m = 6
     off, tgt = off_d.cpu().numpy(), tgt_d.cpu().numpy()
-    n = off.size - 1
-    seed0 = oracle.run_seed(SEED, 0)
-    rng = np.random.default_rng(11)
-    deg = np.diff(off)
-    sample = [int(v) for v in rng.choice(np.nonzero((deg > 0) & (deg < 8))[0], 4)]
-    with H.HyperANF(off_d, tgt_d, log2m, SEED, frontier="auto", profile=True) as h:
-        N0 = h.estimate()[0]
-        for t in (1, 2):
-            h.iterate()
-            for v in sample:
-                got = h.registers(0, v, 1)[0]
-                assert np.array_equal(got, oracle.ball_registers(off, tgt, v, t, log2m, seed0)), (t, v)
-        while h.iterate() > 0:
-            pass
-        final = {v: h.registers(0, v, 1)[0] for v in sample[:2]}
-        T = h.t
+    log2m = 6
+    traj = oracle_trajectory(oracle, off, tgt, log2m, oracle.run_seed(SEED, 0))
+    with H.HyperANF(off_d, tgt_d, log2m, SEED, frontier="auto", use_graph=True,
+                    profile=True) as h:
+        modes = check_every_pass(h, traj)
+        check_graph_driver(h, traj)
+    assert 2 in modes and 3 in modes           # dense and scatter passes both ran
     del off_d, tgt_d
     torch.cuda.empty_cache()
-    for v, got in final.items():
-        assert np.array_equal(got, oracle.ball_registers(off, tgt, v, -1, log2m, seed0)), v
-    assert 1 <= T <= 64
-    c0 = oracle.init(n, log2m, seed0)
-    np.testing.assert_allclose(N0, oracle.sum_sizes(c0), rtol=RTOL)
+
+
+def test_past_2p31_arcs_every_pass(H, oracle):
+    """More arcs than int32 can count: offsets past 2^31 reach the degree
+    classes, the hub segments, the relabelled CSR, the transpose and every
+    pass flavour."""
+    import torch
+    if host_ram_gb() < 40:
+        pytest.skip("needs ~40 GB of free host memory for the oracle")
+    from paper_1011_5599_gb300 import graphs as G
+    off_d, tgt_d = G.rmat_multigraph(25, 65, seed=5, device="cuda")
+    arcs = tgt_d.numel()
+    assert arcs == 65 << 25 and arcs > 2**31
+    off, tgt = off_d.cpu().numpy(), tgt_d.cpu().numpy()
+    assert np.diff(off).max() > 16384           # hub segments
+    log2m = 4
+    traj = oracle_trajectory(oracle, off, tgt, log2m, oracle.run_seed(SEED, 0))
+    del off, tgt
+    seen = set()
+    for kw in (dict(), dict(scatter_den=-1), dict(frontier="off")):
+        with H.HyperANF(off_d, tgt_d, log2m, SEED, use_graph=True, profile=True, **kw) as h:
+            seen |= set(check_every_pass(h, traj))
+            check_graph_driver(h, traj)
+    assert {1, 2, 3} <= seen, seen               # systolic, dense and scatter passes
+    del off_d, tgt_d
+    torch.cuda.empty_cache()

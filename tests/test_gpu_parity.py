@@ -281,14 +281,18 @@ def test_bit_sliced_layout_rejects_unsupported(H):
 
 
 @pytest.mark.parametrize("layout,R", [("byte", 1), ("byte", 4), ("packed", 1)])
-def test_checkpoint_resume_bit_identical(H, layout, R, tmp_path):
+def test_checkpoint_resume_bit_identical(H, oracle, layout, R, tmp_path):
     """Save after some passes, load into a fresh context, resume: counters, T
-    and N(t) equal those of an uninterrupted run."""
+    and N(t) are the oracle's (and so those of an uninterrupted run)."""
     off, tgt = G.rmat(12, seed=17)
     kw = dict(runs=R, layout=layout)
+    ref = [oracle.hyperanf(off, tgt, 6, oracle.run_seed(SEED, r), want_regs=True) for r in range(R)]
+    N_ref = [x[0] for x in ref]
+    T_ref = [x[1] for x in ref]
+    regs_ref = [x[2] for x in ref]
     with H.HyperANF(off, tgt, 6, SEED, **kw) as h:
-        N_ref, T_ref = h.run()
-        regs_ref = [h.registers(r) for r in range(R)]
+        N_run, T_run = h.run()
+        assert list(T_run) == T_ref
     for stop in (0, 1, 3):
         with H.HyperANF(off, tgt, 6, SEED, **kw) as h:
             for _ in range(stop):
@@ -300,10 +304,12 @@ def test_checkpoint_resume_bit_identical(H, layout, R, tmp_path):
             h2.restore(np.fromfile(path, dtype=np.uint8))
             assert h2.t == stop
             N, T = h2.resume()
-            assert list(T) == list(T_ref)
+            assert list(T) == T_ref
             for r in range(R):
-                assert np.array_equal(N[r], N_ref[r])
+                assert np.array_equal(N[r], N_run[r])          # bit-identical to a straight run
+                np.testing.assert_allclose(N[r], N_ref[r], rtol=RTOL, atol=0)
                 assert np.array_equal(h2.registers(r), regs_ref[r])
+                assert h2.digest(r) == oracle.digest(regs_ref[r])
 
 
 def test_resume_after_pass_limit_and_mismatch(H):
@@ -362,6 +368,8 @@ def test_batch_of_graphs_matches_each_alone(H, oracle, R, kw):
         N, T = h.run()
         regs = [[h.registers(r, h.graph_base[g], h.graph_nodes[g]) for r in range(R)]
                 for g in range(len(graphs))]
+        digests = [[h.digest(r, h.graph_base[g], h.graph_nodes[g]) for r in range(R)]
+                   for g in range(len(graphs))]
         assert h.estimate().size == len(graphs) * R
     for g, (off, tgt) in enumerate(graphs):
         for r in range(R):
@@ -370,6 +378,7 @@ def test_batch_of_graphs_matches_each_alone(H, oracle, R, kw):
             assert T[s] == To, (g, r)
             np.testing.assert_allclose(N[s], No, rtol=RTOL, atol=0)
             assert np.array_equal(regs[g][r], ro), (g, r)
+            assert digests[g][r] == oracle.digest(ro), (g, r)
 
 
 def test_batch_checkpoint_and_rejections(H):
@@ -394,3 +403,31 @@ def test_batch_checkpoint_and_rejections(H):
     with pytest.raises(H.HanfError) as e:       # bases must be multiples of 64
         H.HyperANF(*G.empty(100), 6, graph_base=[0, 50, 100], graph_nodes=[50, 50])
     assert e.value.code == H.HANF_EINVAL
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(relabel=False), dict(layout="packed"), dict(runs=4),
+                                dict(runs=2, frontier="off")])
+def test_digest_matches_oracle(H, oracle, kw):
+    """hanf_digest of the counters after two passes, of the whole array and of
+    a ragged node range, equals the oracle's digest of its own counters."""
+    off, tgt = G.web(1 << 12, seed=6)
+    R = kw.get("runs", 1)
+    with H.HyperANF(off, tgt, 6, SEED, **kw) as h:
+        h.iterate()
+        h.iterate()
+        got = [(h.digest(r), h.digest(r, 100, 333), h.digest(r, 4095, 1), h.digest(r, 7, 0))
+               for r in range(R)]
+    for r in range(R):
+        c = oracle.init(off.size - 1, 6, oracle.run_seed(SEED, r))
+        for _ in range(2):
+            c, _ = oracle.union_pass(off, tgt, c)
+        assert got[r] == (oracle.digest(c), oracle.digest(c[100:433]), oracle.digest(c[4095:]), 0)
+
+
+def test_digest_rejects_bad_ranges(H):
+    off, tgt = G.path(10)
+    with H.HyperANF(off, tgt, 4, SEED) as h:
+        for args in ((1, 0, 5), (0, -1, 3), (0, 8, 3)):
+            with pytest.raises(H.HanfError) as e:
+                h.digest(*args)
+            assert e.value.code == H.HANF_EINVAL

@@ -53,8 +53,8 @@ def test_results_same_alone_and_in_the_mix(H, oracle):
         for r in range(R):
             assert np.array_equal(N_a[r], N_s[r])            # bit-identical
         assert info["latency_ms"] >= info["run_ms"] >= 0
-    # and the served results are the oracle's
-    for (N_s, T_s, _), (off, tgt, log2m, R, seed) in list(zip(served, jobs))[:6]:
+    # and every served result is the oracle's
+    for (N_s, T_s, _), (off, tgt, log2m, R, seed) in zip(served, jobs):
         for r in range(R):
             No, To, _ = oracle.hyperanf(off, tgt, log2m, oracle.run_seed(seed, r))
             assert T_s[r] == To
