@@ -52,6 +52,9 @@ WORKLOADS = {
                    text="directed R-MAT scale 24, edge factor 16, m=64, 1 run (profiling case)"),
     "rmat24sym": dict(kind="rmat", scale=24, ef=16, sym=True, log2m=7, runs=1,
                       text="symmetrised R-MAT scale 24, edge factor 16, m=128, 1 run"),
+    "rmat23sym": dict(kind="rmat", scale=23, ef=16, sym=True, log2m=7, runs=1,
+                      text="symmetrised R-MAT scale 23, edge factor 16, m=128, 1 run "
+                           "(profiling case)"),
     "web20": dict(kind="web", n=1 << 20, log2m=6, runs=8,
                   text="web-like n=2^20 (power-law out-degree 2.1, mean 16, host blocks), "
                        "m=64, R=8 runs batched"),
@@ -63,6 +66,7 @@ CPU_SAMPLE = {"rmat27": dict(kind="rmat", scale=22, ef=16, sym=False),
               "rmat22": dict(kind="rmat", scale=18, ef=16, sym=False),
               "rmat24": dict(kind="rmat", scale=19, ef=16, sym=False),
               "rmat24sym": dict(kind="rmat", scale=18, ef=16, sym=True),
+              "rmat23sym": dict(kind="rmat", scale=17, ef=16, sym=True),
               "web20": dict(kind="web", n=1 << 16),
               "er": dict(kind="er", n=10000, arcs=50000)}
 
