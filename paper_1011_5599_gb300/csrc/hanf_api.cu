@@ -78,13 +78,13 @@ struct Sizes {
     int32_t log2m, m, R, W, layout, K, S;
     int32_t d_small, d_hub, history;
     bool copy_graph, transpose, relabel, node_stats;
-    int64_t nwords, nred, ntiles, max_hub, max_seg, scan_elems;
+    int64_t nwords, ntiles, max_hub, max_seg, scan_elems;
 };
 
 struct Layout {
     size_t off, tgt, in_off, in_src, regs0, regs1, F0, F1, cand, cand0, cand1, nodes;
     size_t seg_node, seg_beg, seg_end, hub_first, hub_part, hub_any;
-    size_t blk_part, red_part, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
+    size_t blk_q, est_acc, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
     size_t seg_counts, seg_offs, totals, perm, inv, off2, tgt2, rcounts, roffs, stage;
     size_t ns_prev, ns_dist, ns_reach, ns_ecc, ns_rad;
     size_t slot_T, slot_changed, blk_graph, g_base, g_nodes;
@@ -146,7 +146,6 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     s->relabel = o.relabel != 0 && n > 0 && s->K == 1;
     s->node_stats = o.node_stats != 0;
     s->nwords = std::max<int64_t>(1, (n + 63) / 64);
-    s->nred = (s->nwords + hanf::kEstChunk - 1) / hanf::kEstChunk;
     s->ntiles = hanf::classify_blocks(n);
     s->max_hub = arcs / (s->d_hub + 1) + 1;
     s->max_seg = 2 * (arcs / s->d_hub) + 2;
@@ -187,8 +186,8 @@ Layout make_layout(const Sizes &s)
     L.hub_first = take(4 * (s.max_hub + 1));
     L.hub_part = take((size_t)s.max_seg * s.W);
     L.hub_any = take(s.max_seg);
-    L.blk_part = take(8 * s.nwords * s.R);
-    L.red_part = take(8 * s.nred * s.R);
+    L.blk_q = take(16 * s.nwords * s.R);
+    L.est_acc = take(16 * (size_t)s.S);
     L.hist = take(8 * (size_t)s.history * s.S);
     L.lc = take(8 * (s.m + 1));
     L.seeds = take(8 * (size_t)s.S);
@@ -276,6 +275,7 @@ int reset(hanf_ctx *c, int32_t max_t)
     h.max_t = max_t;
     CU(cudaMemcpyAsync(c->plan.ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemsetAsync(c->plan.slot_T, 0xff, sizeof(int32_t) * c->plan.S, c->stream));   // -1
+    CU(cudaMemsetAsync(c->plan.est_acc, 0, 16 * (size_t)c->plan.S, c->stream));
     CU(hanf::launch_init(c->plan, c->stream));
     int nl = 1;
     CU(hanf::launch_estimate(c->plan, c->stream, &nl));
@@ -366,10 +366,10 @@ int ctl_fail(int32_t err)
 int pass_launch_count(const hanf_ctx *c)
 {
     const Plan &p = c->plan;
+    const bool scatter = !p.layout && p.in_off && p.scatter_den > 0;
     return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
-           (!p.layout && p.W <= 128 ? 1 : 0) +
-           (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0) +
-           (p.K > 1 ? 2 : 3);
+           (!p.layout && p.W <= 128 ? 1 : 0) + (scatter ? 2 : 0) +
+           (scatter && p.est_fused ? 1 : 0) + 2;
 }
 
 }  // namespace
@@ -468,7 +468,6 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.W = s.W;
     p.layout = s.layout;
     p.nwords = s.nwords;
-    p.nred = s.nred;
     p.frontier = o.frontier;
     p.push_den = o.push_den;
     p.dense_den = o.dense_den ? o.dense_den : 2;
@@ -511,8 +510,11 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.nodes = nodes;
     p.hub_part = ws + L.hub_part;
     p.hub_any = ws + L.hub_any;
-    p.blk_part = reinterpret_cast<double *>(ws + L.blk_part);
-    p.red_part = reinterpret_cast<double *>(ws + L.red_part);
+    p.blk_q = reinterpret_cast<unsigned long long *>(ws + L.blk_q);
+    p.est_acc = reinterpret_cast<unsigned long long *>(ws + L.est_acc);
+    // size() changes summed inside the union kernels: byte registers, one
+    // graph, no per-node statistics (those keep the block sums)
+    p.est_fused = (s.layout == 0 && s.K == 1 && !s.node_stats) ? 1 : 0;
     p.hist = reinterpret_cast<double *>(ws + L.hist);
     p.lc = reinterpret_cast<const double *>(ws + L.lc);
     p.seeds = reinterpret_cast<const uint64_t *>(ws + L.seeds);
@@ -914,7 +916,7 @@ struct CkpHeader {
 };
 
 struct CkpParts {
-    size_t header, ctl, regs, bits, hist, blk, slots, total;
+    size_t header, ctl, regs, bits, hist, blk, acc, slots, total;
 };
 
 CkpParts ckp_parts(const hanf_ctx *c)
@@ -926,9 +928,10 @@ CkpParts ckp_parts(const hanf_ctx *c)
     q.regs = (size_t)std::max<int64_t>(p.n, 1) * p.W;
     q.bits = (size_t)p.nwords * 8;
     q.hist = (size_t)p.history_cap * p.S * 8;
-    q.blk = (size_t)p.nwords * p.R * 8;
+    q.blk = (size_t)p.nwords * p.R * 16;
+    q.acc = (size_t)p.S * 16;
     q.slots = (size_t)p.S * 4;
-    q.total = q.header + q.ctl + 2 * q.regs + 2 * q.bits + q.hist + q.blk + q.slots;
+    q.total = q.header + q.ctl + 2 * q.regs + 2 * q.bits + q.hist + q.blk + q.acc + q.slots;
     return q;
 }
 
@@ -936,7 +939,7 @@ CkpHeader ckp_header(const hanf_ctx *c)
 {
     CkpHeader h;
     std::memset(&h, 0, sizeof h);
-    std::memcpy(h.magic, "HANFCKP1", 8);
+    std::memcpy(h.magic, "HANFCKP2", 8);
     h.n = c->plan.n;
     h.arcs = c->plan.arcs;
     h.nwords = c->plan.nwords;
@@ -984,8 +987,10 @@ int hanf_checkpoint_save(hanf_ctx *c, void *buf, size_t bytes)
     CU(cudaMemcpyAsync(d + q.bits, p.F[1], q.bits, cudaMemcpyDeviceToHost, c->stream));
     d += 2 * q.bits;
     CU(cudaMemcpyAsync(d, p.hist, q.hist, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(d + q.hist, p.blk_part, q.blk, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(d + q.hist + q.blk, p.slot_T, q.slots, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(d + q.hist, p.blk_q, q.blk, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(d + q.hist + q.blk, p.est_acc, q.acc, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaMemcpyAsync(d + q.hist + q.blk + q.acc, p.slot_T, q.slots, cudaMemcpyDeviceToHost,
+                       c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return HANF_OK;
 }
@@ -1013,8 +1018,10 @@ int hanf_checkpoint_load(hanf_ctx *c, const void *buf, size_t bytes)
     CU(cudaMemcpyAsync(p.F[1], d + q.bits, q.bits, cudaMemcpyHostToDevice, c->stream));
     d += 2 * q.bits;
     CU(cudaMemcpyAsync(p.hist, d, q.hist, cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemcpyAsync(p.blk_part, d + q.hist, q.blk, cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemcpyAsync(p.slot_T, d + q.hist + q.blk, q.slots, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.blk_q, d + q.hist, q.blk, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.est_acc, d + q.hist + q.blk, q.acc, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(p.slot_T, d + q.hist + q.blk + q.acc, q.slots, cudaMemcpyHostToDevice,
+                       c->stream));
     CU(cudaStreamSynchronize(c->stream));
     c->host_ctl = ctl;
     return HANF_OK;

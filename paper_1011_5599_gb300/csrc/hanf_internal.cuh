@@ -14,7 +14,6 @@ namespace hanf {
 
 constexpr int kMaxRuns = 8;       // R <= 8 runs batched in one counter row
 constexpr int kBlock = 256;       // threads per block of the streaming kernels
-constexpr int kEstChunk = 4096;   // block partials summed by one reduction CTA
 
 // Mutable iteration state, resident in device memory so that a whole
 // HyperANF loop can run as one CUDA graph without the host looking at it.
@@ -45,7 +44,6 @@ struct Plan {
                                       // registers) or 5m/8 (bit-sliced, R = 1)
     int32_t layout;                   // 0 byte registers, 1 five bit-planes
     int64_t nwords;                   // 64-node blocks = bitmap words
-    int64_t nred;                     // first-level reduction CTAs per run
     const int64_t *off;
     const int32_t *tgt;
     const int64_t *in_off;            // transpose (systolic mode), or null
@@ -64,8 +62,14 @@ struct Plan {
     const int32_t *hub_seg_first;     // n_hub + 1 segment offsets
     uint8_t *hub_part;                // n_seg x W partial maxima
     uint8_t *hub_any;                 // n_seg flags: segment merged something
-    double *blk_part;                 // R x nwords estimator partials
-    double *red_part;                 // R x nred
+    // N(t) = sum_v size(c_t[v]), kept exactly in signed 128-bit fixed point
+    // with 52 fractional bits ("Q52"; two 64-bit words, low first)
+    unsigned long long *blk_q;        // R x nwords sums of size() over 64-node blocks
+    unsigned long long *est_acc;      // S running sums N_s(t)
+    int32_t est_fused;                // 1: the union kernels add the size() change of
+                                      // every changed counter to est_acc (byte layout,
+                                      // one graph, no per-node statistics); 0: blocks
+                                      // with a changed counter are summed again
     double *hist;                     // history_cap x S values of N(t)
     const double *lc;                 // m+1 linear-counting values m ln(m/V)
     double amm;                       // alpha_m m^2

@@ -53,14 +53,16 @@ struct Row {
 
 // Register-wise max of four byte registers (Section 3.3, union via broadword
 // programming).  Registers never exceed 31, so bit 7 of every byte is free and
-// serves as the guard bit of the paper's parallel compare: in
-// d = (a | 0x80..80) - b no byte borrows from its neighbour, and bit 7 of byte
-// i of d is set iff a_i >= b_i.  A byte permute that replicates each byte's
-// top bit turns d into the selection mask (0xff where a_i >= b_i), and the
-// result is (a & mask) | (b & ~mask).
+// serves as the guard bit of the paper's parallel compare: setting it is the
+// same as adding 0x80 to every byte, and in d = a + 0x80..80 - b every byte
+// stays within 97..159, so no byte carries into or borrows from its
+// neighbour (one three-input add), and bit 7 of byte i of d is set iff
+// a_i >= b_i.  A byte permute that replicates each byte's top bit turns d
+// into the selection mask (0xff where a_i >= b_i), and the result is
+// (a & mask) | (b & ~mask), one three-input logic operation.
 __device__ __forceinline__ uint32_t bmax(uint32_t a, uint32_t b)
 {
-    const uint32_t d = (a | 0x80808080u) - b;
+    const uint32_t d = a + 0x80808080u - b;
     uint32_t mask;
     // prmt with selector nibbles 8..11: byte i of the result replicates the
     // sign bit of byte i of d (the __byte_perm intrinsic ignores that bit)
@@ -137,6 +139,141 @@ __device__ __forceinline__ uint32_t group_or(uint32_t x)
 __device__ __forceinline__ bool test_bit(const unsigned long long *bits, int32_t v)
 {
     return (__ldg(bits + (v >> 6)) >> (v & 63)) & 1ull;
+}
+
+// ---------------------------------------------------------------- size() and exact N(t)
+
+// size() of a counter (Algorithm 1 with linear counting) from the exact
+// integer S = sum_j 2^(31 - M[j]) over its M registers and the number V of
+// empty registers: S * 2^-31 is exact (S < 2^53), and the division and the
+// product are each rounded once, as IEEE double arithmetic does them.
+__device__ __forceinline__ double size_from_sums(const Plan &p, unsigned long long S, int V, int M)
+{
+    const double sum = (double)S * 0x1p-31;
+    const double Z = 1.0 / sum;
+    double E = p.amm * Z;
+    if (E <= 2.5 * (double)M && V > 0) E = p.lc[V];
+    return E;
+}
+
+// Adds 2^(31 - M) for each of the four byte registers M of w to S, and the
+// number of empty ones to V.  Registers are below 32, so a funnel shift in
+// wrap mode takes its amount (modulo 32) straight from the low bits of the
+// word, byte i after w >> 8i, and mad.wide adds the 32-bit term to the 64-bit
+// sum in one instruction; w + 0x7f..7f sets bit 7 exactly in the non-zero
+// bytes (no byte carries into the next).
+__device__ __forceinline__ void word_sums(uint32_t w, unsigned long long &S, int &V)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        uint32_t term;
+        asm("shf.r.wrap.b32 %0, %1, %2, %3;" : "=r"(term) : "r"(0x80000000u), "r"(0u), "r"(w >> (8 * i)));
+        asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(S) : "r"(term), "r"(1u));
+    }
+    V += __popc(~(w + 0x7f7f7f7fu) & 0x80808080u);
+}
+
+__device__ __forceinline__ void vec_sums(uint4 x, unsigned long long &S, int &V)
+{
+    word_sums(x.x, S, V);
+    word_sums(x.y, S, V);
+    word_sums(x.z, S, V);
+    word_sums(x.w, S, V);
+}
+
+// N(t) = sum_v size(c_t[v]) is kept exactly, as a signed 128-bit integer of
+// units 2^-52 ("Q52").  Every size() value is 0 or lies in (1, 2^40): linear
+// counting gives m ln(m/V) > 1 for V < m registers empty (0 for V = m), and
+// the raw estimate is taken only above 5m/2 or with no empty register, where
+// it exceeds 2 alpha_m m > 20.  So E * 2^52 is an integer below 2^92 and a
+// sum over fewer than 2^31 nodes fits.  Integer addition is exact and
+// commutative: the sum does not depend on the order of the additions (atomics
+// included) and is rounded to double once.
+struct Q128 {
+    unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void q_add(Q128 &a, const Q128 &b)
+{
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(b.lo), "l"(b.hi));
+}
+
+__device__ __forceinline__ void q_sub(Q128 &a, const Q128 &b)
+{
+    asm("sub.cc.u64 %0, %0, %2;\n\tsubc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(b.lo), "l"(b.hi));
+}
+
+// E (0, or in (1, 2^40)) in Q52: mantissa << (exponent - 1023).
+__device__ __forceinline__ Q128 q_from(double E)
+{
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(E);
+    const int ex = (int)(bits >> 52);
+    Q128 q{0ull, 0ull};
+    if (ex == 0) return q;
+    const unsigned long long mant = (bits & ((1ull << 52) - 1ull)) | (1ull << 52);
+    const int sh = ex - 1023;
+    if (sh <= 0) {
+        q.lo = mant >> (-sh);   // 0 < E < 2 (E < 1 does not occur, see above)
+    } else {
+        q.lo = mant << sh;
+        q.hi = mant >> (64 - sh);
+    }
+    return q;
+}
+
+__device__ __forceinline__ Q128 q_shfl_xor(const Q128 &a, int o, unsigned mask = kFull)
+{
+    return Q128{__shfl_xor_sync(mask, a.lo, o), __shfl_xor_sync(mask, a.hi, o)};
+}
+
+// *q += a for a 128-bit value in memory (q[0] low word, q[1] high word).  The
+// carry out of each low-word addition is exactly what that addition adds to
+// the high word, whatever the order the atomics take, so the sum is exact.
+__device__ __forceinline__ void q_atomic_add(unsigned long long *q, const Q128 &a)
+{
+    if ((a.lo | a.hi) == 0ull) return;
+    unsigned long long hi = a.hi;
+    if (a.lo) {
+        const unsigned long long old = atomicAdd(q, a.lo);
+        if (old + a.lo < old) hi += 1ull;
+    }
+    if (hi) atomicAdd(q + 1, hi);
+}
+
+// Round a Q52 value to the nearest double (ties to even): the value itself
+// when it has at most 53 significant bits, else its top 53 bits rounded by
+// the next bit and the bits below it.
+__device__ __forceinline__ double q_to_double(Q128 a)
+{
+    const bool neg = (long long)a.hi < 0;
+    if (neg) {
+        const Q128 z{0ull, 0ull};
+        Q128 t = z;
+        q_sub(t, a);
+        a = t;
+    }
+    double r;
+    if (a.hi == 0ull && a.lo < (1ull << 53)) {
+        r = (double)a.lo * 0x1p-52;
+    } else {
+        const int nb = a.hi ? 128 - __clzll((long long)a.hi) : 64 - __clzll((long long)a.lo);
+        int sh = nb - 53;   // 1 .. 75
+        unsigned long long top = sh >= 64 ? a.hi >> (sh - 64) : (a.lo >> sh) | (a.hi << (64 - sh));
+        const int hb = sh - 1;   // the rounding bit; the sticky bits lie below it
+        const bool half = hb >= 64 ? (a.hi >> (hb - 64)) & 1ull : (a.lo >> hb) & 1ull;
+        bool sticky;
+        if (hb >= 64)
+            sticky = a.lo != 0ull || (hb > 64 && (a.hi & ((1ull << (hb - 64)) - 1ull)) != 0ull);
+        else
+            sticky = hb > 0 && (a.lo & ((1ull << hb) - 1ull)) != 0ull;
+        if (half && (sticky || (top & 1ull))) top += 1ull;
+        if (top == (1ull << 53)) {
+            top >>= 1;
+            sh += 1;
+        }
+        r = (double)top * __longlong_as_double((long long)(1023 + sh - 52) << 52);
+    }
+    return neg ? -r : r;
 }
 
 // ---------------------------------------------------------------- union
@@ -304,10 +441,74 @@ __device__ __forceinline__ void warp_gather(const int32_t *__restrict__ tgt, con
     }
 }
 
+// size(new) - size(old) in Q52 of the run whose 16-byte shares the m/16
+// consecutive lanes of `gmask` around this one hold (`lead`: the lane that
+// takes the result; the others get 0).  Kept out of line: the union kernels
+// call it only for changed counters, and inlined it would raise the register
+// count of their gather loops.
+__device__ __forceinline__ Q128 size_change(const Plan &p, uint4 own, uint4 nw, int runlanes,
+                                         unsigned gmask, bool lead)
+{
+    unsigned long long So = 0, Sn = 0;
+    int Vo = 0, Vn = 0;
+    vec_sums(own, So, Vo);
+    vec_sums(nw, Sn, Vn);
+    for (int o = 1; o < runlanes; o <<= 1) {
+        So += __shfl_xor_sync(gmask, So, o);
+        Sn += __shfl_xor_sync(gmask, Sn, o);
+        Vo += __shfl_xor_sync(gmask, Vo, o);
+        Vn += __shfl_xor_sync(gmask, Vn, o);
+    }
+    Q128 d{0ull, 0ull};
+    if (lead) {
+        d = q_from(size_from_sums(p, Sn, Vn, p.m));
+        q_sub(d, q_from(size_from_sums(p, So, Vo, p.m)));
+    }
+    return d;
+}
+
+// Per-warp shared accumulators of the fused estimate, so that nothing of it
+// stays in registers across a kernel's node loop: the Q52 size() changes of
+// each run, and the in-arcs of the nodes the warp marked changed.
+struct EstShared {
+    unsigned long long q[kMaxRuns][2];
+    unsigned long long cia;
+};
+
+__device__ __forceinline__ EstShared *est_slot()
+{
+    __shared__ EstShared sh[kBlock / 32];
+    return &sh[threadIdx.x >> 5];
+}
+
+// Zero the warp's accumulators (fused estimate); every lane calls it.
+__device__ __forceinline__ void est_begin(const Plan &p)
+{
+    if (!p.est_fused) return;
+    unsigned long long *w = reinterpret_cast<unsigned long long *>(est_slot());
+    const int lane = threadIdx.x & 31;
+    if (lane < 2 * kMaxRuns + 1) w[lane] = 0ull;
+    __syncwarp();
+}
+
+// Add the warp's accumulators to the running sums N_r and to the in-arcs of
+// changed nodes; every lane calls it.
+__device__ __forceinline__ void est_flush(const Plan &p)
+{
+    if (!p.est_fused) return;
+    __syncwarp();
+    const EstShared *e = est_slot();
+    const int lane = threadIdx.x & 31;
+    if (lane < p.R) q_atomic_add(p.est_acc + 2 * lane, Q128{e->q[lane][0], e->q[lane][1]});
+    if (lane == 31 && e->cia) atomicAdd(&p.ctl->changed_in_arcs, e->cia);
+}
+
 // New counter of v = max(acc, c_t[v]); store it if it changed or if v changed
 // in the previous pass (its row in the target buffer is then stale).  Returns
 // the mask of runs whose counter changed (same value on all lanes of the
-// group).  Every lane of the warp must call it.
+// group).  With the fused estimate, size(new) - size(old) of every changed
+// run is added to the warp's accumulator (Algorithm 2's sum s, kept as the
+// previous sum plus the changes).  Every lane of the warp must call it.
 template <int LANES, int VPL>
 __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Row<LANES, VPL> &acc,
                                                 bool need, bool inR, int32_t v, int gl,
@@ -332,6 +533,20 @@ __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Ro
         if (gl == 0) ++c_write;
     }
     if (need && gl == 0) ++c_own;
+    if (p.est_fused && mask) {
+        // the m/16 lanes of a run (consecutive in the group) sum their 16-byte
+        // shares; the first of them turns the sums into size() values
+        const int lane = threadIdx.x & 31;
+        const unsigned gmask = LANES == 32 ? kFull : (((1u << LANES) - 1u) << (lane - gl));
+        const int runlanes = p.m >> 4;
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) {
+            const int run = ((k * LANES + gl) << 4) >> p.b;
+            const bool lead = (gl & (runlanes - 1)) == 0 && ((mask >> run) & 1u);
+            const Q128 d = size_change(p, own.v[k], nw.v[k], runlanes, gmask, lead);
+            if (lead) q_atomic_add(est_slot()->q[run], d);
+        }
+    }
     return mask;
 }
 
@@ -389,7 +604,11 @@ __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, i
     if (bal == 0) return;
     const int lane = threadIdx.x & 31;
     if (lane == 0) mt.nodes += __popc(bal);
-    if (ch) atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
+    if (ch) {
+        atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
+        if (p.est_fused && p.in_off)   // the next pass's flavour depends on these
+            atomicAdd(&est_slot()->cia, (unsigned long long)(p.in_off[v + 1] - p.in_off[v]));
+    }
     tally_runs(p, ch, bal, v, mask, mt);
 }
 
@@ -451,6 +670,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
+    est_begin(p);
     // systolic passes visit the small-degree candidates only
     const int32_t *list = push ? p.cand_list[0] : p.nodes;
     const int64_t count = push ? (int64_t)ctl->cand_count[0] : p.n_small;
@@ -495,6 +715,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
     flush_counters(p, cur, mt, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
+    est_flush(p);
 }
 
 // Union pass over medium nodes (a warp per node) and hub segments (a warp
@@ -520,6 +741,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
+    est_begin(p);
     for (int64_t it = warp; it < total; it += nwarps) {
         const bool seg = it < p.n_seg;
         const int32_t v = seg ? __ldg(p.seg_node + it) : __ldg(med + (it - p.n_seg));
@@ -546,6 +768,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
         }
     }
     flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
+    est_flush(p);
 }
 
 // ---------------------------------------------------------------- asynchronous gathers
@@ -614,6 +837,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
+    est_begin(p);
 
     // ---- producer state (warp-uniform) ----
     int64_t p_it = warp - nwarps, p_e = 0, p_end = 0;
@@ -720,6 +944,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     }
     cp_async_wait<0>();
     flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
+    est_flush(p);
 }
 
 // Small-degree union with asynchronous row copies (gather_variant 3; rows of
@@ -758,6 +983,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small_async(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
+    est_begin(p);
     const int32_t *list = p.nodes;
     const int64_t count = p.n_small;
     const int64_t stride = nwarps * GPW;
@@ -839,6 +1065,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small_async(Plan p)
     }
     cp_async_wait<0>();
     flush_counters(p, cur, mt, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
+    est_flush(p);
 }
 
 // Hub nodes: combine the segment partials written by k_union_warp, then
@@ -858,6 +1085,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_own = 0, c_write = 0;
     MarkTally mt;
+    est_begin(p);
     for (int64_t base = warp * GPW; base < p.n_hub; base += nwarps * GPW) {
         const int64_t h = base + g;
         const bool valid = h < p.n_hub;
@@ -882,6 +1110,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
     flush_counters(p, cur, mt, 0u, 0u, c_own, c_write);
+    est_flush(p);
 }
 
 // ---------------------------------------------------------------- pass control
@@ -1197,7 +1426,12 @@ __device__ __forceinline__ void scatter_entries(const Plan &p, int cur, int32_t 
                 if (bal) {
                     if (ch) {
                         const unsigned long long bit = 1ull << (vs[u] & 63);
-                        if ((atomicOr(&p.F[cur ^ 1][vs[u] >> 6], bit) & bit) == 0ull) ++mt.fresh;
+                        if ((atomicOr(&p.F[cur ^ 1][vs[u] >> 6], bit) & bit) == 0ull) {
+                            ++mt.fresh;
+                            if (p.est_fused)
+                                atomicAdd(&est_slot()->cia, (unsigned long long)(p.in_off[vs[u] + 1] -
+                                                                                 p.in_off[vs[u]]));
+                        }
                     }
                     tally_runs(p, ch, bal, vs[u], mask, mt);
                 }
@@ -1227,6 +1461,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_scatter(Plan p)
     const int64_t total = nseg + p.nwords;
     uint32_t pairs = 0, raised = 0;
     MarkTally mt;
+    est_begin(p);
     bool bad = false;
     for (int64_t it = warp; it < total; it += nwarps) {
         if (it < nseg) {
@@ -1260,6 +1495,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_scatter(Plan p)
         }
     }
     flush_counters(p, cur, mt, pairs, pairs, pairs, raised);
+    est_flush(p);
     if (bad) p.ctl->err = HANF_ESTATE;
 }
 
@@ -1307,12 +1543,9 @@ __global__ void k_post(Plan p, cudaGraphConditionalHandle h, int use_cond)
 
 // ---------------------------------------------------------------- estimator
 
-// size() of run r of node v (Algorithm 1 with linear counting).  The sum of
-// 2^-M[j] is exact: it is accumulated as the integer sum of 2^(31-M[j]).  M
+// size() of run r of node v (Algorithm 1 with linear counting).  M
 // registers a run, known at compile time so that a lane issues all of its
-// loads before it adds; zero registers are counted a 32-bit word at a time
-// (with the registers below 32, bit 7 of each byte is free: after setting it,
-// subtracting 1 per byte clears it exactly in the bytes that were 0).
+// loads before it adds.
 template <int M>
 __device__ __forceinline__ double node_size(const Plan &p, const uint8_t *rc, int64_t v, int r)
 {
@@ -1323,21 +1556,8 @@ __device__ __forceinline__ double node_size(const Plan &p, const uint8_t *rc, in
     unsigned long long S = 0;
     int V = 0;
 #pragma unroll
-    for (int k = 0; k < M / 16; ++k) {
-        const uint32_t w4[4] = {x[k].x, x[k].y, x[k].z, x[k].w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t z = (w4[j] | 0x80808080u) - 0x01010101u;
-            V += __popc(~z & 0x80808080u);
-#pragma unroll
-            for (int s = 0; s < 32; s += 8) S += 0x80000000u >> ((w4[j] >> s) & 0xffu);
-        }
-    }
-    const double sum = (double)S * 0x1p-31;
-    const double Z = 1.0 / sum;
-    double E = p.amm * Z;
-    if (E <= 2.5 * (double)M && V > 0) E = p.lc[V];
-    return E;
+    for (int k = 0; k < M / 16; ++k) vec_sums(x[k], S, V);
+    return size_from_sums(p, S, V, M);
 }
 
 // Per-node statistics of the sequence E_v(0..T) (the radius distribution and
@@ -1371,17 +1591,26 @@ __device__ __forceinline__ void node_stats_update(const Plan &p, int r, int64_t 
         p.ns_rad[i] = t;
 }
 
-// Per 64-node block and run: sum of size() over the block, recomputed only
-// for blocks with a counter changed by the last pass (Section 3.3, harmonic
-// partial sums of small blocks).  A warp per (run, block); the warp sum uses
-// a fixed butterfly, so the partial is a deterministic function of the
-// block's registers.
+// Slot of a (run, 64-node block) item: the run, or in a batch graph * R + run.
+__device__ __forceinline__ int item_slot(const Plan &p, int r, int64_t blk)
+{
+    return p.K > 1 ? __ldg(p.blk_graph + blk) * p.R + r : r;
+}
+
+// Per 64-node block and run: the exact sum of size() over the block
+// (Section 3.3, harmonic partial sums of small blocks), recomputed at t = 0
+// and afterwards only for blocks with a counter changed by the last pass;
+// the change of each block sum goes into the running sum of its slot.  A warp
+// per (run, block); lane 0 keeps the warp's running change and adds it to
+// the slot whenever the slot changes.  With the fused estimate this only runs
+// at t = 0.
 template <int M>
 __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
 {
     DevCtl *c = p.ctl;
     if (c->done) return;
     const bool all = c->t == 0;
+    if (p.est_fused && !all) return;
     const uint8_t *rc = p.regs[c->parity];
     const unsigned long long *Fc = p.F[c->parity];
     const int lane = threadIdx.x & 31;
@@ -1389,6 +1618,8 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long cia = 0;   // in-arcs of changed nodes, flushed once
     const int64_t items = p.nwords * p.R;
+    Q128 run_q{0ull, 0ull};       // lane 0: change not yet added to slot run_slot
+    int run_slot = -1;
     for (int64_t it = warp; it < items; it += nwarps) {
         const int r = (int)(it / p.nwords);
         const int64_t blk = it - (int64_t)r * p.nwords;
@@ -1416,71 +1647,85 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
             if (v0 < lim) node_stats_update(p, r, v0, e0, all, c->t);
             if (v1 < lim) node_stats_update(p, r, v1, e1, all, c->t);
         }
-        double s = e0 + e1;
+        Q128 s = q_from(e0);
+        q_add(s, q_from(e1));
 #pragma unroll
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (lane == 0) p.blk_part[it] = s;
+        for (int o = 16; o; o >>= 1) q_add(s, q_shfl_xor(s, o));
+        const int slot = item_slot(p, r, blk);
+        if (lane == 0) {
+            unsigned long long *bq = p.blk_q + 2 * it;
+            Q128 d = s;
+            if (!all) q_sub(d, Q128{bq[0], bq[1]});
+            bq[0] = s.lo;
+            bq[1] = s.hi;
+            if (slot != run_slot) {
+                if (run_slot >= 0) q_atomic_add(p.est_acc + 2 * run_slot, run_q);
+                run_q = Q128{0ull, 0ull};
+                run_slot = slot;
+            }
+            q_add(run_q, d);
+        }
     }
-    if (lane == 0 && cia) atomicAdd(&p.ctl->changed_in_arcs, cia);
+    if (lane == 0) {
+        if (run_slot >= 0) q_atomic_add(p.est_acc + 2 * run_slot, run_q);
+        if (cia) atomicAdd(&p.ctl->changed_in_arcs, cia);
+    }
 }
 
-// Fixed-shape tree over the block partials: first level, one CTA per run and
-// kEstChunk consecutive blocks.
-__global__ void __launch_bounds__(kBlock) k_est_reduce1(Plan p)
+// Fused estimate, scatter passes: the pushes raise counters word by word, so
+// the size() change of each counter the pass changed (bitmap F_{t+1}) is
+// taken after the pushes, from its old row (c_t) and its new one (c_{t+1}).
+// A warp per (run, bitmap word); runs the pass left unchanged add zero.
+template <int M>
+__global__ void __launch_bounds__(kBlock) k_est_changed(Plan p)
 {
-    __shared__ double sh[kBlock];
     const DevCtl *c = p.ctl;
-    if (c->done) return;
-    const int r = blockIdx.y;
-    const int64_t i0 = (int64_t)blockIdx.x * kEstChunk;
-    double s = 0.0;
-    for (int j = threadIdx.x; j < kEstChunk; j += kBlock) {
-        const int64_t i = i0 + j;
-        if (i < p.nwords) s += p.blk_part[(int64_t)r * p.nwords + i];
+    if (c->done || !p.est_fused || c->mode != kModeScatter) return;
+    const int cur = c->parity;
+    const uint8_t *ro = p.regs[cur], *rn = p.regs[cur ^ 1];
+    const unsigned long long *Fn = p.F[cur ^ 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t items = p.nwords * p.R;
+    Q128 q{0ull, 0ull};
+    int run = -1;
+    for (int64_t it = warp; it < items; it += nwarps) {
+        const int r = (int)(it / p.nwords);
+        const int64_t blk = it - (int64_t)r * p.nwords;
+        const unsigned long long word = Fn[blk];
+        if (word == 0ull) continue;
+        if (r != run) {   // warp-uniform
+#pragma unroll
+            for (int o = 16; o; o >>= 1) q_add(q, q_shfl_xor(q, o));
+            if (lane == 0 && run >= 0) q_atomic_add(p.est_acc + 2 * run, q);
+            q = Q128{0ull, 0ull};
+            run = r;
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t v = blk * 64 + lane + 32 * h;
+            if ((word >> (lane + 32 * h)) & 1ull) {
+                Q128 d = q_from(node_size<M>(p, rn, v, r));
+                q_sub(d, q_from(node_size<M>(p, ro, v, r)));
+                q_add(q, d);
+            }
+        }
     }
-    sh[threadIdx.x] = s;
-    for (int w = kBlock / 2; w; w >>= 1) {
-        __syncthreads();
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    }
-    if (threadIdx.x == 0) p.red_part[(int64_t)r * p.nred + blockIdx.x] = sh[0];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) q_add(q, q_shfl_xor(q, o));
+    if (lane == 0 && run >= 0) q_atomic_add(p.est_acc + 2 * run, q);
 }
 
-// Batches: N(t) of slot (graph g, run r) = fixed-shape sum of g's block
-// partials, one CTA per slot.
-__global__ void __launch_bounds__(kBlock) k_est_reduce_graphs(Plan p)
+// N_s(t) of every slot into the history: its running sum rounded to double.
+__global__ void k_est_finalize(Plan p)
 {
-    __shared__ double sh[kBlock];
     const DevCtl *c = p.ctl;
     if (c->done) return;
-    const int slot = blockIdx.x;
-    const int g = slot / p.R, r = slot - g * p.R;
-    const int64_t b0 = p.g_base[g] >> 6, b1 = (p.g_base[g + 1] + 63) >> 6;
-    double s = 0.0;
-    for (int64_t b = b0 + threadIdx.x; b < b1; b += kBlock) s += p.blk_part[(int64_t)r * p.nwords + b];
-    sh[threadIdx.x] = s;
-    for (int w = kBlock / 2; w; w >>= 1) {
-        __syncthreads();
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    }
-    if (threadIdx.x == 0) p.hist[(int64_t)c->t * p.S + slot] = sh[0];
-}
-
-// Second level: N(t) of run r into the history.
-__global__ void __launch_bounds__(kBlock) k_est_reduce2(Plan p)
-{
-    __shared__ double sh[kBlock];
-    const DevCtl *c = p.ctl;
-    if (c->done) return;
-    const int r = blockIdx.x;
-    double s = 0.0;
-    for (int64_t i = threadIdx.x; i < p.nred; i += kBlock) s += p.red_part[(int64_t)r * p.nred + i];
-    sh[threadIdx.x] = s;
-    for (int w = kBlock / 2; w; w >>= 1) {
-        __syncthreads();
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    }
-    if (threadIdx.x == 0) p.hist[(int64_t)c->t * p.S + r] = sh[0];
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < p.S;
+         s += (int64_t)gridDim.x * blockDim.x)
+        p.hist[(int64_t)c->t * p.S + s] =
+            q_to_double(Q128{p.est_acc[2 * s], p.est_acc[2 * s + 1]});
 }
 
 // ---------------------------------------------------------------- init
@@ -2172,11 +2417,7 @@ __device__ __forceinline__ double pnode_size(const Plan &p, const uint8_t *rc, i
             S += (unsigned long long)__popc(sel) << (31 - M);
         }
     }
-    const double sum = (double)S * 0x1p-31;
-    const double Z = 1.0 / sum;
-    double E = p.amm * Z;
-    if (E <= 2.5 * (double)p.m && V > 0) E = p.lc[V];
-    return E;
+    return size_from_sums(p, S, V, p.m);
 }
 
 template <int P>
@@ -2191,6 +2432,8 @@ __global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long cia = 0;   // in-arcs of changed nodes, flushed once
+    Q128 run_q{0ull, 0ull};       // lane 0: change not yet added to slot run_slot
+    int run_slot = -1;
     for (int64_t blk = warp; blk < p.nwords; blk += nwarps) {
         if (!all && Fc[blk] == 0ull) continue;
         const int64_t v0 = blk * 64 + lane, v1 = v0 + 32;
@@ -2214,12 +2457,29 @@ __global__ void __launch_bounds__(kBlock) k_pest_blocks(Plan p)
             if (v0 < lim) node_stats_update(p, 0, v0, e0, all, c->t);
             if (v1 < lim) node_stats_update(p, 0, v1, e1, all, c->t);
         }
-        double s = e0 + e1;
+        Q128 s = q_from(e0);
+        q_add(s, q_from(e1));
 #pragma unroll
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (lane == 0) p.blk_part[blk] = s;
+        for (int o = 16; o; o >>= 1) q_add(s, q_shfl_xor(s, o));
+        const int slot = item_slot(p, 0, blk);
+        if (lane == 0) {
+            unsigned long long *bq = p.blk_q + 2 * blk;
+            Q128 d = s;
+            if (!all) q_sub(d, Q128{bq[0], bq[1]});
+            bq[0] = s.lo;
+            bq[1] = s.hi;
+            if (slot != run_slot) {
+                if (run_slot >= 0) q_atomic_add(p.est_acc + 2 * run_slot, run_q);
+                run_q = Q128{0ull, 0ull};
+                run_slot = slot;
+            }
+            q_add(run_q, d);
+        }
     }
-    if (lane == 0 && cia) atomicAdd(&p.ctl->changed_in_arcs, cia);
+    if (lane == 0) {
+        if (run_slot >= 0) q_atomic_add(p.est_acc + 2 * run_slot, run_q);
+        if (cia) atomicAdd(&p.ctl->changed_in_arcs, cia);
+    }
 }
 
 // Algorithm 2's initialisation in the packed layout: node v adds itself.
@@ -2567,13 +2827,22 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
         default: return cudaErrorInvalidValue;
         }
     }
-    if (p.K > 1) {
-        k_est_reduce_graphs<<<p.S, kBlock, 0, s>>>(p);
-        if (nlaunch) *nlaunch += 2;
-    } else {
-        k_est_reduce1<<<dim3((unsigned)p.nred, (unsigned)p.R), kBlock, 0, s>>>(p);
-        k_est_reduce2<<<p.R, kBlock, 0, s>>>(p);
-        if (nlaunch) *nlaunch += 3;
+    k_est_finalize<<<grid_for(p.S, kBlock, 152), kBlock, 0, s>>>(p);
+    if (nlaunch) *nlaunch += 2;
+    return cudaGetLastError();
+}
+
+// Fused estimate: the size() changes of a scatter pass, after its pushes.
+cudaError_t launch_est_changed(const Plan &p, cudaStream_t s)
+{
+    const int g = grid_for(p.nwords * p.R, kBlock / 32, 152 * 16);
+    switch (p.m) {
+    case 16: k_est_changed<16><<<g, kBlock, 0, s>>>(p); break;
+    case 32: k_est_changed<32><<<g, kBlock, 0, s>>>(p); break;
+    case 64: k_est_changed<64><<<g, kBlock, 0, s>>>(p); break;
+    case 128: k_est_changed<128><<<g, kBlock, 0, s>>>(p); break;
+    case 256: k_est_changed<256><<<g, kBlock, 0, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -2607,12 +2876,17 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     }
     if (err != cudaSuccess) return err;
     if (ev1) cudaEventRecord(ev1, s);
+    const bool est_scatter = p.est_fused && !p.layout && p.in_off && p.scatter_den > 0;
+    if (est_scatter) {
+        err = launch_est_changed(p, s);
+        if (err != cudaSuccess) return err;
+    }
     if (p.S > 8) k_slot_T<<<grid_for(p.S, kBlock, 152 * 4), kBlock, 0, s>>>(p);
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
     if (nlaunch)
         *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
                     (!p.layout && p.W <= 128 ? 1 : 0) +
-                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0);
+                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0) + (est_scatter ? 1 : 0);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_estimate(p, s, nlaunch);
