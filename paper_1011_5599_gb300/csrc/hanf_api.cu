@@ -77,14 +77,14 @@ struct Sizes {
     int64_t n, arcs;
     int32_t log2m, m, R, W, layout, K, S;
     int32_t d_small, d_hub, history;
-    bool copy_graph, transpose, relabel, node_stats;
+    bool copy_graph, transpose, relabel, node_stats, est_fused;
     int64_t nwords, ntiles, max_hub, max_seg, scan_elems;
 };
 
 struct Layout {
     size_t off, tgt, in_off, in_src, regs0, regs1, F0, F1, cand, cand0, cand1, nodes;
     size_t seg_node, seg_beg, seg_end, hub_first, hub_part, hub_any;
-    size_t blk_q, est_acc, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
+    size_t blk_q, est_acc, ecache, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
     size_t seg_counts, seg_offs, totals, perm, inv, off2, tgt2, rcounts, roffs, stage;
     size_t ns_prev, ns_dist, ns_reach, ns_ecc, ns_rad;
     size_t slot_T, slot_changed, blk_graph, g_base, g_nodes;
@@ -145,6 +145,9 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
     s->S = s->K * s->R;
     s->relabel = o.relabel != 0 && n > 0 && s->K == 1;
     s->node_stats = o.node_stats != 0;
+    // only the changed counters' size() is evaluated after a pass (one graph,
+    // byte registers, no per-node statistics, which keep the block sums)
+    s->est_fused = s->layout == 0 && s->K == 1 && !s->node_stats;
     s->nwords = std::max<int64_t>(1, (n + 63) / 64);
     s->ntiles = hanf::classify_blocks(n);
     s->max_hub = arcs / (s->d_hub + 1) + 1;
@@ -188,6 +191,7 @@ Layout make_layout(const Sizes &s)
     L.hub_any = take(s.max_seg);
     L.blk_q = take(16 * s.nwords * s.R);
     L.est_acc = take(16 * (size_t)s.S);
+    L.ecache = s.est_fused ? take(8 * rows * (size_t)s.R) : 0;
     L.hist = take(8 * (size_t)s.history * s.S);
     L.lc = take(8 * (s.m + 1));
     L.seeds = take(8 * (size_t)s.S);
@@ -368,8 +372,7 @@ int pass_launch_count(const hanf_ctx *c)
     const Plan &p = c->plan;
     const bool scatter = !p.layout && p.in_off && p.scatter_den > 0;
     return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
-           (!p.layout && p.W <= 128 ? 1 : 0) + (scatter ? 2 : 0) +
-           (scatter && p.est_fused ? 1 : 0) + 2;
+           (!p.layout && p.W <= 128 ? 1 : 0) + (scatter ? 2 : 0) + (p.est_fused ? 3 : 2);
 }
 
 }  // namespace
@@ -512,9 +515,8 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.hub_any = ws + L.hub_any;
     p.blk_q = reinterpret_cast<unsigned long long *>(ws + L.blk_q);
     p.est_acc = reinterpret_cast<unsigned long long *>(ws + L.est_acc);
-    // size() changes summed inside the union kernels: byte registers, one
-    // graph, no per-node statistics (those keep the block sums)
-    p.est_fused = (s.layout == 0 && s.K == 1 && !s.node_stats) ? 1 : 0;
+    p.est_fused = s.est_fused ? 1 : 0;
+    p.ecache = s.est_fused ? reinterpret_cast<double *>(ws + L.ecache) : nullptr;
     p.hist = reinterpret_cast<double *>(ws + L.hist);
     p.lc = reinterpret_cast<const double *>(ws + L.lc);
     p.seeds = reinterpret_cast<const uint64_t *>(ws + L.seeds);
@@ -916,7 +918,7 @@ struct CkpHeader {
 };
 
 struct CkpParts {
-    size_t header, ctl, regs, bits, hist, blk, acc, slots, total;
+    size_t header, ctl, regs, bits, hist, blk, acc, cache, slots, total;
 };
 
 CkpParts ckp_parts(const hanf_ctx *c)
@@ -930,8 +932,10 @@ CkpParts ckp_parts(const hanf_ctx *c)
     q.hist = (size_t)p.history_cap * p.S * 8;
     q.blk = (size_t)p.nwords * p.R * 16;
     q.acc = (size_t)p.S * 16;
+    q.cache = p.est_fused ? (size_t)std::max<int64_t>(p.n, 1) * p.R * 8 : 0;
     q.slots = (size_t)p.S * 4;
-    q.total = q.header + q.ctl + 2 * q.regs + 2 * q.bits + q.hist + q.blk + q.acc + q.slots;
+    q.total = q.header + q.ctl + 2 * q.regs + 2 * q.bits + q.hist + q.blk + q.acc + q.cache +
+              q.slots;
     return q;
 }
 
@@ -989,8 +993,11 @@ int hanf_checkpoint_save(hanf_ctx *c, void *buf, size_t bytes)
     CU(cudaMemcpyAsync(d, p.hist, q.hist, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(d + q.hist, p.blk_q, q.blk, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaMemcpyAsync(d + q.hist + q.blk, p.est_acc, q.acc, cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaMemcpyAsync(d + q.hist + q.blk + q.acc, p.slot_T, q.slots, cudaMemcpyDeviceToHost,
-                       c->stream));
+    if (q.cache)
+        CU(cudaMemcpyAsync(d + q.hist + q.blk + q.acc, p.ecache, q.cache, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CU(cudaMemcpyAsync(d + q.hist + q.blk + q.acc + q.cache, p.slot_T, q.slots,
+                       cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     return HANF_OK;
 }
@@ -1020,8 +1027,11 @@ int hanf_checkpoint_load(hanf_ctx *c, const void *buf, size_t bytes)
     CU(cudaMemcpyAsync(p.hist, d, q.hist, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(p.blk_q, d + q.hist, q.blk, cudaMemcpyHostToDevice, c->stream));
     CU(cudaMemcpyAsync(p.est_acc, d + q.hist + q.blk, q.acc, cudaMemcpyHostToDevice, c->stream));
-    CU(cudaMemcpyAsync(p.slot_T, d + q.hist + q.blk + q.acc, q.slots, cudaMemcpyHostToDevice,
-                       c->stream));
+    if (q.cache)
+        CU(cudaMemcpyAsync(p.ecache, d + q.hist + q.blk + q.acc, q.cache, cudaMemcpyHostToDevice,
+                           c->stream));
+    CU(cudaMemcpyAsync(p.slot_T, d + q.hist + q.blk + q.acc + q.cache, q.slots,
+                       cudaMemcpyHostToDevice, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     c->host_ctl = ctl;
     return HANF_OK;

@@ -66,10 +66,12 @@ struct Plan {
     // with 52 fractional bits ("Q52"; two 64-bit words, low first)
     unsigned long long *blk_q;        // R x nwords sums of size() over 64-node blocks
     unsigned long long *est_acc;      // S running sums N_s(t)
-    int32_t est_fused;                // 1: the union kernels add the size() change of
-                                      // every changed counter to est_acc (byte layout,
-                                      // one graph, no per-node statistics); 0: blocks
-                                      // with a changed counter are summed again
+    int32_t est_fused;                // 1: after each pass only the changed counters'
+                                      // size() is evaluated, its change added to
+                                      // est_acc (byte layout, one graph, no per-node
+                                      // statistics); 0: blocks with a changed counter
+                                      // are summed again
+    double *ecache;                   // est_fused: R x n, size() of every counter
     double *hist;                     // history_cap x S values of N(t)
     const double *lc;                 // m+1 linear-counting values m ln(m/V)
     double amm;                       // alpha_m m^2

@@ -145,14 +145,19 @@ __device__ __forceinline__ bool test_bit(const unsigned long long *bits, int32_t
 
 // size() of a counter (Algorithm 1 with linear counting) from the exact
 // integer S = sum_j 2^(31 - M[j]) over its M registers and the number V of
-// empty registers: S * 2^-31 is exact (S < 2^53), and the division and the
-// product are each rounded once, as IEEE double arithmetic does them.
+// empty registers.  sum = S * 2^-31 is exact (M <= S < 2^40); it is built
+// from the bits of S, and E <= 5m/2 is decided on the bit patterns of the two
+// positive doubles, so that only the division and the product use the
+// (narrow, on this GPU) double-precision pipe; each is rounded once, as IEEE
+// double arithmetic does it.
 __device__ __forceinline__ double size_from_sums(const Plan &p, unsigned long long S, int V, int M)
 {
-    const double sum = (double)S * 0x1p-31;
-    const double Z = 1.0 / sum;
+    const int L = 64 - __clzll((long long)S);   // S in [2^(L-1), 2^L)
+    const unsigned long long sum_bits = ((unsigned long long)(1023 + L - 1 - 31) << 52) |
+                                        ((S << (53 - L)) & ((1ull << 52) - 1ull));
+    const double Z = 1.0 / __longlong_as_double((long long)sum_bits);
     double E = p.amm * Z;
-    if (E <= 2.5 * (double)M && V > 0) E = p.lc[V];
+    if (__double_as_longlong(E) <= __double_as_longlong(2.5 * (double)M) && V > 0) E = p.lc[V];
     return E;
 }
 
@@ -441,74 +446,10 @@ __device__ __forceinline__ void warp_gather(const int32_t *__restrict__ tgt, con
     }
 }
 
-// size(new) - size(old) in Q52 of the run whose 16-byte shares the m/16
-// consecutive lanes of `gmask` around this one hold (`lead`: the lane that
-// takes the result; the others get 0).  Kept out of line: the union kernels
-// call it only for changed counters, and inlined it would raise the register
-// count of their gather loops.
-__device__ __forceinline__ Q128 size_change(const Plan &p, uint4 own, uint4 nw, int runlanes,
-                                         unsigned gmask, bool lead)
-{
-    unsigned long long So = 0, Sn = 0;
-    int Vo = 0, Vn = 0;
-    vec_sums(own, So, Vo);
-    vec_sums(nw, Sn, Vn);
-    for (int o = 1; o < runlanes; o <<= 1) {
-        So += __shfl_xor_sync(gmask, So, o);
-        Sn += __shfl_xor_sync(gmask, Sn, o);
-        Vo += __shfl_xor_sync(gmask, Vo, o);
-        Vn += __shfl_xor_sync(gmask, Vn, o);
-    }
-    Q128 d{0ull, 0ull};
-    if (lead) {
-        d = q_from(size_from_sums(p, Sn, Vn, p.m));
-        q_sub(d, q_from(size_from_sums(p, So, Vo, p.m)));
-    }
-    return d;
-}
-
-// Per-warp shared accumulators of the fused estimate, so that nothing of it
-// stays in registers across a kernel's node loop: the Q52 size() changes of
-// each run, and the in-arcs of the nodes the warp marked changed.
-struct EstShared {
-    unsigned long long q[kMaxRuns][2];
-    unsigned long long cia;
-};
-
-__device__ __forceinline__ EstShared *est_slot()
-{
-    __shared__ EstShared sh[kBlock / 32];
-    return &sh[threadIdx.x >> 5];
-}
-
-// Zero the warp's accumulators (fused estimate); every lane calls it.
-__device__ __forceinline__ void est_begin(const Plan &p)
-{
-    if (!p.est_fused) return;
-    unsigned long long *w = reinterpret_cast<unsigned long long *>(est_slot());
-    const int lane = threadIdx.x & 31;
-    if (lane < 2 * kMaxRuns + 1) w[lane] = 0ull;
-    __syncwarp();
-}
-
-// Add the warp's accumulators to the running sums N_r and to the in-arcs of
-// changed nodes; every lane calls it.
-__device__ __forceinline__ void est_flush(const Plan &p)
-{
-    if (!p.est_fused) return;
-    __syncwarp();
-    const EstShared *e = est_slot();
-    const int lane = threadIdx.x & 31;
-    if (lane < p.R) q_atomic_add(p.est_acc + 2 * lane, Q128{e->q[lane][0], e->q[lane][1]});
-    if (lane == 31 && e->cia) atomicAdd(&p.ctl->changed_in_arcs, e->cia);
-}
-
 // New counter of v = max(acc, c_t[v]); store it if it changed or if v changed
 // in the previous pass (its row in the target buffer is then stale).  Returns
 // the mask of runs whose counter changed (same value on all lanes of the
-// group).  With the fused estimate, size(new) - size(old) of every changed
-// run is added to the warp's accumulator (Algorithm 2's sum s, kept as the
-// previous sum plus the changes).  Every lane of the warp must call it.
+// group).  Every lane of the warp must call it.
 template <int LANES, int VPL>
 __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Row<LANES, VPL> &acc,
                                                 bool need, bool inR, int32_t v, int gl,
@@ -533,20 +474,6 @@ __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Ro
         if (gl == 0) ++c_write;
     }
     if (need && gl == 0) ++c_own;
-    if (p.est_fused && mask) {
-        // the m/16 lanes of a run (consecutive in the group) sum their 16-byte
-        // shares; the first of them turns the sums into size() values
-        const int lane = threadIdx.x & 31;
-        const unsigned gmask = LANES == 32 ? kFull : (((1u << LANES) - 1u) << (lane - gl));
-        const int runlanes = p.m >> 4;
-#pragma unroll
-        for (int k = 0; k < VPL; ++k) {
-            const int run = ((k * LANES + gl) << 4) >> p.b;
-            const bool lead = (gl & (runlanes - 1)) == 0 && ((mask >> run) & 1u);
-            const Q128 d = size_change(p, own.v[k], nw.v[k], runlanes, gmask, lead);
-            if (lead) q_atomic_add(est_slot()->q[run], d);
-        }
-    }
     return mask;
 }
 
@@ -604,11 +531,7 @@ __device__ __forceinline__ void warp_mark(const Plan &p, int cur, bool leader, i
     if (bal == 0) return;
     const int lane = threadIdx.x & 31;
     if (lane == 0) mt.nodes += __popc(bal);
-    if (ch) {
-        atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
-        if (p.est_fused && p.in_off)   // the next pass's flavour depends on these
-            atomicAdd(&est_slot()->cia, (unsigned long long)(p.in_off[v + 1] - p.in_off[v]));
-    }
+    if (ch) atomicOr(&p.F[cur ^ 1][v >> 6], 1ull << (v & 63));
     tally_runs(p, ch, bal, v, mask, mt);
 }
 
@@ -670,7 +593,6 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
-    est_begin(p);
     // systolic passes visit the small-degree candidates only
     const int32_t *list = push ? p.cand_list[0] : p.nodes;
     const int64_t count = push ? (int64_t)ctl->cand_count[0] : p.n_small;
@@ -715,7 +637,6 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
     flush_counters(p, cur, mt, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
-    est_flush(p);
 }
 
 // Union pass over medium nodes (a warp per node) and hub segments (a warp
@@ -741,7 +662,6 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
-    est_begin(p);
     for (int64_t it = warp; it < total; it += nwarps) {
         const bool seg = it < p.n_seg;
         const int32_t v = seg ? __ldg(p.seg_node + it) : __ldg(med + (it - p.n_seg));
@@ -768,7 +688,6 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
         }
     }
     flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
-    est_flush(p);
 }
 
 // ---------------------------------------------------------------- asynchronous gathers
@@ -837,7 +756,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
-    est_begin(p);
 
     // ---- producer state (warp-uniform) ----
     int64_t p_it = warp - nwarps, p_e = 0, p_end = 0;
@@ -944,7 +862,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     }
     cp_async_wait<0>();
     flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
-    est_flush(p);
 }
 
 // Small-degree union with asynchronous row copies (gather_variant 3; rows of
@@ -983,7 +900,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small_async(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
-    est_begin(p);
     const int32_t *list = p.nodes;
     const int64_t count = p.n_small;
     const int64_t stride = nwarps * GPW;
@@ -1065,7 +981,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small_async(Plan p)
     }
     cp_async_wait<0>();
     flush_counters(p, cur, mt, c_scan, gl == 0 ? c_gather : 0u, c_own, c_write);
-    est_flush(p);
 }
 
 // Hub nodes: combine the segment partials written by k_union_warp, then
@@ -1085,7 +1000,6 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_own = 0, c_write = 0;
     MarkTally mt;
-    est_begin(p);
     for (int64_t base = warp * GPW; base < p.n_hub; base += nwarps * GPW) {
         const int64_t h = base + g;
         const bool valid = h < p.n_hub;
@@ -1110,7 +1024,6 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
     flush_counters(p, cur, mt, 0u, 0u, c_own, c_write);
-    est_flush(p);
 }
 
 // ---------------------------------------------------------------- pass control
@@ -1426,12 +1339,7 @@ __device__ __forceinline__ void scatter_entries(const Plan &p, int cur, int32_t 
                 if (bal) {
                     if (ch) {
                         const unsigned long long bit = 1ull << (vs[u] & 63);
-                        if ((atomicOr(&p.F[cur ^ 1][vs[u] >> 6], bit) & bit) == 0ull) {
-                            ++mt.fresh;
-                            if (p.est_fused)
-                                atomicAdd(&est_slot()->cia, (unsigned long long)(p.in_off[vs[u] + 1] -
-                                                                                 p.in_off[vs[u]]));
-                        }
+                        if ((atomicOr(&p.F[cur ^ 1][vs[u] >> 6], bit) & bit) == 0ull) ++mt.fresh;
                     }
                     tally_runs(p, ch, bal, vs[u], mask, mt);
                 }
@@ -1461,7 +1369,6 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_scatter(Plan p)
     const int64_t total = nseg + p.nwords;
     uint32_t pairs = 0, raised = 0;
     MarkTally mt;
-    est_begin(p);
     bool bad = false;
     for (int64_t it = warp; it < total; it += nwarps) {
         if (it < nseg) {
@@ -1495,7 +1402,6 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_scatter(Plan p)
         }
     }
     flush_counters(p, cur, mt, pairs, pairs, pairs, raised);
-    est_flush(p);
     if (bad) p.ctl->err = HANF_ESTATE;
 }
 
@@ -1602,8 +1508,8 @@ __device__ __forceinline__ int item_slot(const Plan &p, int r, int64_t blk)
 // and afterwards only for blocks with a counter changed by the last pass;
 // the change of each block sum goes into the running sum of its slot.  A warp
 // per (run, block); lane 0 keeps the warp's running change and adds it to
-// the slot whenever the slot changes.  With the fused estimate this only runs
-// at t = 0.
+// the slot whenever the slot changes.  With the changed-node estimate
+// (k_est_changed) this only runs at t = 0, and also fills its cache.
 template <int M>
 __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
 {
@@ -1647,6 +1553,10 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
             if (v0 < lim) node_stats_update(p, r, v0, e0, all, c->t);
             if (v1 < lim) node_stats_update(p, r, v1, e1, all, c->t);
         }
+        if (p.est_fused) {   // t = 0: every node's size(), for k_est_changed
+            if (v0 < lim) p.ecache[(int64_t)r * p.n + v0] = e0;
+            if (v1 < lim) p.ecache[(int64_t)r * p.n + v1] = e1;
+        }
         Q128 s = q_from(e0);
         q_add(s, q_from(e1));
 #pragma unroll
@@ -1672,49 +1582,82 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
     }
 }
 
-// Fused estimate, scatter passes: the pushes raise counters word by word, so
-// the size() change of each counter the pass changed (bitmap F_{t+1}) is
-// taken after the pushes, from its old row (c_t) and its new one (c_{t+1}).
-// A warp per (run, bitmap word); runs the pass left unchanged add zero.
+// Changed-node estimate (one graph, byte registers, no per-node
+// statistics): after a pass, only the counters it changed (bitmap F_{t+1})
+// can change size(), so only they are evaluated, and N changes by their
+// size(new) - size(old), size(old) being kept per node and run in a cache.
+// The changed nodes of a warp's bitmap words are packed into a queue in
+// shared memory and taken 32 at a time, a node per lane, so the
+// double-precision work runs on full warps.  Also sums the in-arcs of the
+// changed nodes (the share of arcs whose successor changed picks the next
+// pass's flavour).
+constexpr int kQueue = 96;   // < 32 left over + 64 from one bitmap word
+
 template <int M>
 __global__ void __launch_bounds__(kBlock) k_est_changed(Plan p)
 {
-    const DevCtl *c = p.ctl;
-    if (c->done || !p.est_fused || c->mode != kModeScatter) return;
-    const int cur = c->parity;
-    const uint8_t *ro = p.regs[cur], *rn = p.regs[cur ^ 1];
-    const unsigned long long *Fn = p.F[cur ^ 1];
-    const int lane = threadIdx.x & 31;
+    DevCtl *c = p.ctl;
+    if (c->done || !p.est_fused || c->t == 0) return;
+    __shared__ int32_t queue[kBlock / 32][kQueue];
+    __shared__ unsigned long long wsum[kBlock / 32][kMaxRuns][2];
+    const uint8_t *rc = p.regs[c->parity];
+    const unsigned long long *Fc = p.F[c->parity];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t items = p.nwords * p.R;
-    Q128 q{0ull, 0ull};
-    int run = -1;
-    for (int64_t it = warp; it < items; it += nwarps) {
-        const int r = (int)(it / p.nwords);
-        const int64_t blk = it - (int64_t)r * p.nwords;
-        const unsigned long long word = Fn[blk];
-        if (word == 0ull) continue;
-        if (r != run) {   // warp-uniform
+    int32_t *q = queue[wib];
+    if (lane < 2 * kMaxRuns) (&wsum[wib][0][0])[lane] = 0ull;
+    __syncwarp();
+    unsigned long long cia = 0;
+    int cnt = 0;   // queued nodes (warp-uniform)
+    // nodes q[cnt - k .. cnt), one per lane k > lane
+    auto drain = [&](int k) {
+        const bool on = lane < k;
+        const int32_t v = on ? q[cnt - k + lane] : 0;
+        __syncwarp();
+        if (on && p.in_off) cia += (unsigned long long)(p.in_off[v + 1] - p.in_off[v]);
+        for (int r = 0; r < p.R; ++r) {
+            Q128 d{0ull, 0ull};
+            if (on) {
+                const double E = node_size<M>(p, rc, v, r);
+                double *ce = p.ecache + (int64_t)r * p.n + v;
+                const double old = *ce;
+                if (__double_as_longlong(E) != __double_as_longlong(old)) {
+                    d = q_from(E);
+                    q_sub(d, q_from(old));
+                    *ce = E;
+                }
+            }
 #pragma unroll
-            for (int o = 16; o; o >>= 1) q_add(q, q_shfl_xor(q, o));
-            if (lane == 0 && run >= 0) q_atomic_add(p.est_acc + 2 * run, q);
-            q = Q128{0ull, 0ull};
-            run = r;
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t v = blk * 64 + lane + 32 * h;
-            if ((word >> (lane + 32 * h)) & 1ull) {
-                Q128 d = q_from(node_size<M>(p, rn, v, r));
-                q_sub(d, q_from(node_size<M>(p, ro, v, r)));
-                q_add(q, d);
+            for (int o = 16; o; o >>= 1) q_add(d, q_shfl_xor(d, o));
+            if (lane == 0) {
+                Q128 t{wsum[wib][r][0], wsum[wib][r][1]};
+                q_add(t, d);
+                wsum[wib][r][0] = t.lo;
+                wsum[wib][r][1] = t.hi;
             }
         }
-    }
+        cnt -= k;
+    };
+    for (int64_t w = warp; w < p.nwords; w += nwarps) {
+        const unsigned long long bits = Fc[w];
+        if (bits == 0ull) continue;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) q_add(q, q_shfl_xor(q, o));
-    if (lane == 0 && run >= 0) q_atomic_add(p.est_acc + 2 * run, q);
+        for (int h = 0; h < 2; ++h) {
+            const bool b = (bits >> (32 * h + lane)) & 1ull;
+            const unsigned bal = __ballot_sync(kFull, b);
+            if (b) q[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)(w * 64 + 32 * h + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        while (cnt >= 32) drain(32);
+    }
+    if (cnt > 0) drain(cnt);
+    __syncwarp();
+    if (lane < p.R) q_atomic_add(p.est_acc + 2 * lane, Q128{wsum[wib][lane][0], wsum[wib][lane][1]});
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cia += __shfl_xor_sync(kFull, cia, o);
+    if (lane == 0 && cia) atomicAdd(&c->changed_in_arcs, cia);
 }
 
 // N_s(t) of every slot into the history: its running sum rounded to double.
@@ -2808,6 +2751,8 @@ cudaError_t launch_init(const Plan &p, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_est_changed(const Plan &p, cudaStream_t s);
+
 cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
 {
     if (p.layout) {
@@ -2827,15 +2772,19 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
         default: return cudaErrorInvalidValue;
         }
     }
+    if (p.est_fused) {
+        const cudaError_t err = launch_est_changed(p, s);
+        if (err != cudaSuccess) return err;
+    }
     k_est_finalize<<<grid_for(p.S, kBlock, 152), kBlock, 0, s>>>(p);
-    if (nlaunch) *nlaunch += 2;
+    if (nlaunch) *nlaunch += p.est_fused ? 3 : 2;
     return cudaGetLastError();
 }
 
-// Fused estimate: the size() changes of a scatter pass, after its pushes.
+// Changed-node estimate (returns at once at t = 0).
 cudaError_t launch_est_changed(const Plan &p, cudaStream_t s)
 {
-    const int g = grid_for(p.nwords * p.R, kBlock / 32, 152 * 16);
+    const int g = grid_for(p.nwords, kBlock / 32, 152 * 8);
     switch (p.m) {
     case 16: k_est_changed<16><<<g, kBlock, 0, s>>>(p); break;
     case 32: k_est_changed<32><<<g, kBlock, 0, s>>>(p); break;
@@ -2876,17 +2825,12 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     }
     if (err != cudaSuccess) return err;
     if (ev1) cudaEventRecord(ev1, s);
-    const bool est_scatter = p.est_fused && !p.layout && p.in_off && p.scatter_den > 0;
-    if (est_scatter) {
-        err = launch_est_changed(p, s);
-        if (err != cudaSuccess) return err;
-    }
     if (p.S > 8) k_slot_T<<<grid_for(p.S, kBlock, 152 * 4), kBlock, 0, s>>>(p);
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
     if (nlaunch)
         *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
                     (!p.layout && p.W <= 128 ? 1 : 0) +
-                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0) + (est_scatter ? 1 : 0);
+                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_estimate(p, s, nlaunch);
