@@ -446,13 +446,14 @@ __device__ __forceinline__ void warp_gather(const int32_t *__restrict__ tgt, con
     }
 }
 
-// New counter of v = max(acc, c_t[v]); store it if it changed or if v changed
-// in the previous pass (its row in the target buffer is then stale).  Returns
+// New counter of v = max(acc, c_t[v]); store it if it changed or if `stale`
+// (v changed in the previous pass, or t = 0, when the target buffer holds
+// only the rows of nodes without arcs).  Returns
 // the mask of runs whose counter changed (same value on all lanes of the
 // group).  Every lane of the warp must call it.
 template <int LANES, int VPL>
 __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Row<LANES, VPL> &acc,
-                                                bool need, bool inR, int32_t v, int gl,
+                                                bool need, bool stale, int32_t v, int gl,
                                                 uint32_t &c_own, uint32_t &c_write,
                                                 const Row<LANES, VPL> *pre = nullptr)
 {
@@ -469,7 +470,7 @@ __device__ __forceinline__ uint32_t node_finish(const Plan &p, int cur, const Ro
         }
     }
     mask = group_or<LANES>(mask);
-    if (need && (mask || inR)) {
+    if (need && (mask || stale)) {
         row_store(p.regs[cur ^ 1], v, nw, gl);
         if (gl == 0) ++c_write;
     }
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
         }
         const bool inR = valid && !first && test_bit(Fc, v);
         const bool need = valid && (any || inR);
-        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write,
+        const uint32_t mask = node_finish(p, cur, acc, need, inR || first, v, gl, c_own, c_write,
                                           own_early ? &own : nullptr);
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
         } else {
             const bool inR = take && !first && test_bit(Fc, v);
             const bool need = take && (any || inR) && g == 0;
-            const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+            const uint32_t mask = node_finish(p, cur, acc, need, inR || first, v, gl, c_own, c_write);
             warp_mark(p, cur, lane == 0, v, mask, mt);
         }
     }
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
                 const int32_t v = __ldg(med + (m.item - p.n_seg));
                 const bool inR = !first && test_bit(Fc, v);
                 const bool need = (anyw || inR) && g == 0;
-                const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+                const uint32_t mask = node_finish(p, cur, acc, need, inR || first, v, gl, c_own, c_write);
                 warp_mark(p, cur, lane == 0, v, mask, mt);
             }
             row_zero(acc);
@@ -976,7 +977,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small_async(Plan p)
         const bool any = len > 0;
         const bool inR = valid && !first && test_bit(Fc, v);
         const bool need = valid && (any || inR);
-        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write, &own);
+        const uint32_t mask = node_finish(p, cur, acc, need, inR || first, v, gl, c_own, c_write, &own);
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
     cp_async_wait<0>();
@@ -1020,7 +1021,7 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
         }
         const bool inR = take && !first && test_bit(Fc, v);
         const bool need = take && (any || inR);
-        const uint32_t mask = node_finish(p, cur, acc, need, inR, v, gl, c_own, c_write);
+        const uint32_t mask = node_finish(p, cur, acc, need, inR || first, v, gl, c_own, c_write);
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
     flush_counters(p, cur, mt, 0u, 0u, c_own, c_write);
@@ -1508,15 +1509,14 @@ __device__ __forceinline__ int item_slot(const Plan &p, int r, int64_t blk)
 // and afterwards only for blocks with a counter changed by the last pass;
 // the change of each block sum goes into the running sum of its slot.  A warp
 // per (run, block); lane 0 keeps the warp's running change and adds it to
-// the slot whenever the slot changes.  With the changed-node estimate
-// (k_est_changed) this only runs at t = 0, and also fills its cache.
+// the slot whenever the slot changes.  Not used with the changed-node
+// estimate (k_est_first, k_est_changed).
 template <int M>
 __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
 {
     DevCtl *c = p.ctl;
     if (c->done) return;
     const bool all = c->t == 0;
-    if (p.est_fused && !all) return;
     const uint8_t *rc = p.regs[c->parity];
     const unsigned long long *Fc = p.F[c->parity];
     const int lane = threadIdx.x & 31;
@@ -1553,10 +1553,6 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
             if (v0 < lim) node_stats_update(p, r, v0, e0, all, c->t);
             if (v1 < lim) node_stats_update(p, r, v1, e1, all, c->t);
         }
-        if (p.est_fused) {   // t = 0: every node's size(), for k_est_changed
-            if (v0 < lim) p.ecache[(int64_t)r * p.n + v0] = e0;
-            if (v1 < lim) p.ecache[(int64_t)r * p.n + v1] = e1;
-        }
         Q128 s = q_from(e0);
         q_add(s, q_from(e1));
 #pragma unroll
@@ -1592,6 +1588,29 @@ __global__ void __launch_bounds__(kBlock) k_est_blocks(Plan p)
 // changed nodes (the share of arcs whose successor changed picks the next
 // pass's flavour).
 constexpr int kQueue = 96;   // < 32 left over + 64 from one bitmap word
+
+// Changed-node estimate at t = 0: every counter holds its own node only, one
+// register at rho+ >= 1 and m - 1 empty, so its raw estimate
+// alpha_m m^2 / (m - 1 + 2^-rho+) is below 5m/2 and size() is linear
+// counting's m ln(m / (m - 1)) for every node: the cache gets that value and
+// N(0) = n m ln(m / (m - 1)), exactly in Q52 (a value below 2 has at most 53
+// bits there, and n < 2^31).
+__global__ void __launch_bounds__(kBlock) k_est_first(Plan p)
+{
+    const DevCtl *c = p.ctl;
+    if (c->done || !p.est_fused || c->t != 0) return;
+    const double E0 = p.lc[p.m - 1];
+    const int64_t cells = p.n * p.R;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cells;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p.ecache[i] = E0;
+    if (blockIdx.x == 0 && threadIdx.x < p.R) {
+        const Q128 q = q_from(E0);
+        const unsigned long long n = (unsigned long long)p.n;
+        p.est_acc[2 * threadIdx.x] = q.lo * n;
+        p.est_acc[2 * threadIdx.x + 1] = __umul64hi(q.lo, n);
+    }
+}
 
 template <int M>
 __global__ void __launch_bounds__(kBlock) k_est_changed(Plan p)
@@ -1676,7 +1695,9 @@ __global__ void k_est_finalize(Plan p)
 // Algorithm 2's initialisation: every counter empty, then node v adds itself
 // (Algorithm 1's add): register h_b(v) <- min(rho+(h^b(v)), 31) with
 // h = splitmix64(v XOR seed_r).  One thread per 16-byte chunk of the counter
-// array; both ping-pong buffers get c_0.
+// array.  regs[0] gets c_0; regs[1] (the target of pass 0) only the rows of
+// nodes without arcs, which no pass visits: pass 0 stores the row of every
+// node it visits.
 __global__ void __launch_bounds__(kBlock) k_init(Plan p)
 {
     const int64_t cpr = p.W >> 4;
@@ -1704,7 +1725,7 @@ __global__ void __launch_bounds__(kBlock) k_init(Plan p)
         if (rel >= 0 && rel < 16) w[rel >> 2] = (uint32_t)rho << ((rel & 3) * 8);
         const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
         reinterpret_cast<uint4 *>(p.regs[0])[c] = val;
-        reinterpret_cast<uint4 *>(p.regs[1])[c] = val;
+        if (__ldg(p.off + v + 1) == __ldg(p.off + v)) reinterpret_cast<uint4 *>(p.regs[1])[c] = val;
     }
 }
 
@@ -2755,7 +2776,11 @@ cudaError_t launch_est_changed(const Plan &p, cudaStream_t s);
 
 cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
 {
-    if (p.layout) {
+    if (p.est_fused) {
+        k_est_first<<<grid_for(p.n * p.R, kBlock, 152 * 16), kBlock, 0, s>>>(p);
+        const cudaError_t err = launch_est_changed(p, s);
+        if (err != cudaSuccess) return err;
+    } else if (p.layout) {
         cudaError_t err = with_planes(p.m, [&](auto P) {
             k_pest_blocks<decltype(P)::value><<<grid_for(p.nwords, kBlock / 32, 152 * 64), kBlock, 0, s>>>(p);
             return cudaGetLastError();
@@ -2771,10 +2796,6 @@ cudaError_t launch_estimate(const Plan &p, cudaStream_t s, int *nlaunch)
         case 256: k_est_blocks<256><<<g, kBlock, 0, s>>>(p); break;
         default: return cudaErrorInvalidValue;
         }
-    }
-    if (p.est_fused) {
-        const cudaError_t err = launch_est_changed(p, s);
-        if (err != cudaSuccess) return err;
     }
     k_est_finalize<<<grid_for(p.S, kBlock, 152), kBlock, 0, s>>>(p);
     if (nlaunch) *nlaunch += p.est_fused ? 3 : 2;
