@@ -117,6 +117,13 @@ typedef struct hanf_opts {
                               arcs/scatter_den in-arcs (byte layout); 0 = 8
                               for rows of at most 128 bytes (R*m), never for
                               wider rows; negative = never                   */
+    int64_t l2_hot_bytes;  /* > 0: keep up to this many bytes of the hottest
+                              counter rows (stored first, by in-degree class)
+                              of the buffer a pass reads in the L2's
+                              persisting set-aside (an access-policy window on
+                              the union launches; the context's persisting-L2
+                              limit is raised for the context's lifetime and
+                              restored by hanf_destroy); 0 = off            */
 } hanf_opts;
 
 /* Fill *opts with the defaults above. */

@@ -259,6 +259,8 @@ struct hanf_ctx {
     std::vector<double> trace;   // 8 values per pass (hanf_trace)
     const int32_t *perm;         // input id -> stored row (relabelled), or null
     uint8_t *stage;              // staging rows for relabelled register reads
+    size_t l2_window;            // bytes of hot rows kept persisting in L2 (0 = off)
+    size_t l2_limit_before;      // the context's persisting-L2 limit before create
 };
 
 namespace {
@@ -292,13 +294,39 @@ int reset(hanf_ctx *c, int32_t max_t)
     return HANF_OK;
 }
 
+// Access-policy window over the hottest rows of the buffer the coming pass
+// reads (stored first), or none (bytes = 0).
+int set_l2_window(hanf_ctx *c, const void *base, size_t bytes)
+{
+    cudaStreamAttrValue v;
+    std::memset(&v, 0, sizeof v);
+    v.accessPolicyWindow.base_ptr = const_cast<void *>(base);
+    v.accessPolicyWindow.num_bytes = bytes;
+    v.accessPolicyWindow.hitRatio = bytes ? 1.0f : 0.0f;
+    v.accessPolicyWindow.hitProp = bytes ? cudaAccessPropertyPersisting : cudaAccessPropertyNormal;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    CU(cudaStreamSetAttribute(c->stream, cudaStreamAttributeAccessPolicyWindow, &v));
+    if (c->fork.side)
+        CU(cudaStreamSetAttribute(c->fork.side, cudaStreamAttributeAccessPolicyWindow, &v));
+    return HANF_OK;
+}
+
 int one_pass(hanf_ctx *c)
 {
     const bool prof = c->opts.profile != 0;
     const DevCtl before = c->host_ctl;
     int nl = 0;
-    CU(hanf::launch_pass(c->plan, c->stream, 0, 0, prof ? c->ev[0] : nullptr,
-                         prof ? c->ev[1] : nullptr, &nl, &c->fork));
+    if (c->l2_window) {
+        const int rc = set_l2_window(c, c->plan.regs[c->host_ctl.parity], c->l2_window);
+        if (rc) return rc;
+    }
+    const cudaError_t le = hanf::launch_pass(c->plan, c->stream, 0, 0, prof ? c->ev[0] : nullptr,
+                                             prof ? c->ev[1] : nullptr, &nl, &c->fork);
+    if (c->l2_window) {
+        const int rc = set_l2_window(c, nullptr, 0);
+        if (rc) return rc;
+    }
+    CU(le);
     c->launches += nl;
     int rc = read_ctl(c);
     if (rc) return rc;
@@ -666,6 +694,26 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
                        s.W <= 128 && hanf::small_async_blocks(s.W) > 0)
                           ? 3
                           : 0;
+
+    if (o.l2_hot_bytes > 0 && s.layout == 0) {
+        // persisting L2 lines for the hottest counter rows (host-loop driver)
+        int max_persist = 0, max_window = 0;
+        size_t before = 0;
+        if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev) !=
+                cudaSuccess ||
+            cudaDeviceGetLimit(&before, cudaLimitPersistingL2CacheSize) != cudaSuccess)
+            return bail(fail(HANF_ECUDA, "L2 persistence queries failed"));
+        const size_t want = std::min<size_t>({(size_t)o.l2_hot_bytes, (size_t)max_persist,
+                                              (size_t)max_window, (size_t)std::max<int64_t>(n, 1) * s.W});
+        if (want > 0) {
+            if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::max(want, before)) != cudaSuccess)
+                return bail(fail(HANF_ECUDA, "cannot set the persisting L2 limit"));
+            c->l2_window = want;
+            c->l2_limit_before = before;
+        }
+    }
 
     rc = reset(c, s.history);
     if (rc) return bail(rc);
@@ -1157,6 +1205,10 @@ void hanf_destroy(hanf_ctx *c)
     if (c->fork.join) cudaEventDestroy(c->fork.join);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->l2_window) {
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->l2_limit_before);
+    }
     delete c;
 }
 

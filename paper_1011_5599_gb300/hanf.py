@@ -64,7 +64,7 @@ class Opts(ctypes.Structure):
                 ("graph_nodes", ctypes.POINTER(ctypes.c_int64)),
                 ("graph_seeds", ctypes.POINTER(ctypes.c_uint64)),
                 ("seeds", ctypes.POINTER(ctypes.c_uint64)), ("stream", ctypes.c_void_p),
-                ("scatter_den", ctypes.c_int32)]
+                ("scatter_den", ctypes.c_int32), ("l2_hot_bytes", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -169,9 +169,11 @@ def default_opts() -> Opts:
 def make_opts(runs=1, frontier="auto", push_den=4, small_max_deg=0, hub_min_deg=0,
               history_cap=0, use_graph=False, profile=False, seeds=None, stream=None,
               dense_den=0, relabel=True, gather_variant=0, layout=0, node_stats=False,
-              graph_base=None, graph_nodes=None, graph_seeds=None, scatter_den=0):
+              graph_base=None, graph_nodes=None, graph_seeds=None, scatter_den=0,
+              l2_hot_bytes=0):
     o = default_opts()
     o.scatter_den = scatter_den
+    o.l2_hot_bytes = int(l2_hot_bytes)
     o.runs = runs
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
     o.push_den = push_den
@@ -275,7 +277,7 @@ class HyperANF:
                  profile: bool = False, seeds=None, device=None, stream=None,
                  dense_den: int = 0, relabel: bool = True, gather_variant: int = 0,
                  layout=0, node_stats: bool = False, graph_base=None, graph_nodes=None,
-                 graph_seeds=None, scatter_den: int = 0):
+                 graph_seeds=None, scatter_den: int = 0, l2_hot_bytes: int = 0):
         import torch
 
         self.device = torch.device(device if device is not None else "cuda")
@@ -305,7 +307,7 @@ class HyperANF:
                                                 seeds, self.stream.cuda_stream, dense_den,
                                                 relabel, gather_variant, layout, node_stats,
                                                 graph_base, graph_nodes, graph_seeds,
-                                                scatter_den)
+                                                scatter_den, l2_hot_bytes)
         self.K = 1 if graph_nodes is None else len(graph_nodes)
         self.S = self.K * runs
         self.graph_base = graph_base
