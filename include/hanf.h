@@ -88,14 +88,13 @@ typedef struct hanf_opts {
                               order (hot counters share cache lines); results
                               and hanf_registers use input ids either way    */
     int32_t gather_variant;/* how rows are gathered: 1 = register batches in
-                              every kernel; 3 = asynchronous copies into
+                              every kernel; 2 = asynchronous copies into a
+                              shared-memory ring for medium-degree nodes and
+                              hub segments; 3 = asynchronous copies into
                               per-lane shared-memory slots in the small-degree
-                              kernel's dense passes; 2 = that, and bulk (TMA)
-                              copies of whole rows into a shared-memory ring,
-                              completed on transaction barriers, for
-                              medium-degree nodes and hub segments; 0 = the
-                              default, 3 for rows of at most 128 bytes (2 and
-                              3 apply to such rows only), 1 otherwise         */
+                              kernel's dense passes; 0 = the default, 3 for
+                              rows of at most 128 bytes (2 and 3 apply to such
+                              rows only), 1 otherwise                         */
     int32_t layout;        /* 0 = one byte per register; 1 = five bit-planes of
                               m bits (5m/8 bytes per counter; runs = 1 and
                               m >= 32); results are identical               */

@@ -392,8 +392,6 @@ int ctl_fail(int32_t err)
     if (err == HANF_ESTATE)
         return fail(HANF_ESTATE, "a scatter pass exceeded its compare-and-swap bound "
                                  "(registers outside 0..31)");
-    if (err == HANF_ETIMEOUT)
-        return fail(HANF_ETIMEOUT, "a bulk-copy wait in a union kernel exceeded its bound");
     return fail(err, "history capacity exhausted");
 }
 
@@ -692,7 +690,7 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.warp_variant = (o.gather_variant == 2 && p.union_async_warps > 0) ? 2 : 1;
     // asynchronous copies in the small-degree kernel by default (rows of at
     // most 128 bytes; measured 26.4 -> 25.1 ms a dense R-MAT 27 pass)
-    p.small_variant = ((o.gather_variant == 0 || o.gather_variant >= 2) && !s.layout &&
+    p.small_variant = ((o.gather_variant == 0 || o.gather_variant == 3) && !s.layout &&
                        s.W <= 128 && hanf::small_async_blocks(s.W) > 0)
                           ? 3
                           : 0;
@@ -832,7 +830,7 @@ int drive(hanf_ctx *c, double *N_out, int32_t cap, int32_t *T_out, int32_t max_i
             N_out[(int64_t)r * cap + t] = t < have ? hist[(size_t)t * S + r] : 0.0;
         T_out[r] = slotT[r] >= 0 ? slotT[r] : T;
     }
-    if (h.err == HANF_ESTATE || h.err == HANF_ETIMEOUT) return ctl_fail(h.err);
+    if (h.err == HANF_ESTATE) return ctl_fail(h.err);
     if (h.err) return fail(HANF_ERANGE, "no stabilisation within %d passes / %d values", max_iter, cap);
     return HANF_OK;
 }

@@ -709,112 +709,36 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// ---------------------------------------------------------------- bulk-copy gathers
-
-__device__ __forceinline__ unsigned smem_u32(const void *ptr)
-{
-    return (unsigned)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_inval(unsigned long long *bar)
-{
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Arrive on the barrier and add `bytes` to the transaction count its current
-// phase waits for.
-__device__ __forceinline__ void mbar_arrive_tx(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// One bounded look at the barrier: true once its phase of the given parity
-// has completed.
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bulk (TMA) copy of `bytes` (a multiple of 16, both addresses 16-byte
-// aligned) from this GPU's global memory into this CTA's shared memory; its
-// bytes count against the barrier's transaction count when they land.
-__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
-                                          unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Shared memory written by generic stores or read by generic loads before an
-// asynchronous copy reuses it.
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// try_wait rounds (each may suspend the warp for a while) before a wait is
-// declared stuck: the copies only read this GPU's memory and always complete,
-// so the bound is never reached in a correct run.
-constexpr int kWaitLimit = 1 << 22;
-
-// Pipeline of the bulk-copy warp kernel: D stages of 32 rows per warp, each
-// with its transaction barrier and its bookkeeping.
-struct StageMeta {
-    int64_t item;     // work item the stage belongs to, -1 if empty
-    uint32_t valid;   // lanes whose target row was copied
-    int32_t last;     // 1 if it is the item's last stage
-};
-
+// Pipeline depth (stages of 32 arcs in the shared-memory ring of a warp).
 template <int LANES>
-struct BulkCfg {
+struct AsyncCfg {
     static constexpr int W = 16 * LANES;
-    static constexpr int D = W <= 64 ? 4 : 3;
-    static constexpr size_t rows_per_warp = (size_t)D * 32 * W;
-    // padded to 128 bytes: every warp's rows start 16-byte aligned, as bulk
-    // copies require
-    static constexpr size_t smem_per_warp =
-        (rows_per_warp + D * (8 + sizeof(StageMeta)) + 127) / 128 * 128;
+    static constexpr int D = W <= 64 ? 4 : 2;
+    static constexpr size_t smem_per_warp = (size_t)D * 32 * W;
     static constexpr size_t smem_per_block = smem_per_warp * (kBlock / 32);
 };
 
-// Union pass over medium nodes and hub segments with the row gathers done by
-// bulk copies (gather_variant 2; rows of at most 128 bytes): every warp
-// streams its work items as stages of up to 32 arcs; lane i copies the whole
-// row of the stage's i-th successor into shared memory with one bulk copy
-// (the stage's transaction barrier counts the bytes), the targets of a stage
-// are loaded one stage ahead, and D-1 stages are in flight while the oldest
-// is merged.  Successors that fail the changed-bitmap test are not copied;
-// the stage's valid mask tells the merge which rows are there.  A wait that
-// exceeds its bound sets HANF_ETIMEOUT in the control block.
+// Per-stage bookkeeping kept in shared memory next to the ring.
+struct StageMeta {
+    int64_t item;   // work item the stage belongs to, -1 if empty
+    int32_t valid;  // rows actually gathered
+    int32_t last;   // 1 if it is the item's last stage
+};
+
+// Union pass over medium nodes and hub segments with the row gathers in
+// flight as asynchronous copies: every warp streams its work items as stages
+// of up to 32 arcs; the targets of a stage are loaded one stage ahead, the
+// rows of D-1 stages are in flight while the oldest is merged from shared
+// memory.  Rows of skipped successors are zero-filled, the identity of max.
+// For rows of at most 128 bytes (LANES <= 8, one vector per lane).
 template <int LANES>
-__global__ void __launch_bounds__(kBlock, 2) k_union_warp_bulk(Plan p)
+__global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
 {
-    using Cfg = BulkCfg<LANES>;
-    static_assert(Cfg::smem_per_warp % 16 == 0 && Cfg::W % 16 == 0 && (32 * Cfg::W) % 16 == 0,
-                  "bulk copies need 16-byte aligned shared-memory rows");
+    using Cfg = AsyncCfg<LANES>;
     constexpr int GPW = 32 / LANES;
     constexpr int D = Cfg::D;
     static_assert(GPW * LANES == 32, "lane groups tile the warp");
-    extern __shared__ __align__(128) uint8_t bulk_smem[];
+    extern __shared__ uint4 smem_raw[];
     const DevCtl *ctl = p.ctl;
     if (ctl->done || ctl->mode == kModeScatter) return;
     const int cur = ctl->parity;
@@ -827,18 +751,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_bulk(Plan p)
     const int64_t total = p.n_seg + (push ? (int64_t)ctl->cand_count[1] : p.n_med);
     const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
     const int wib = threadIdx.x >> 5;
-    uint8_t *ring = bulk_smem + (size_t)wib * Cfg::smem_per_warp;
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(ring + Cfg::rows_per_warp);
-    StageMeta *meta = reinterpret_cast<StageMeta *>(bar + D);
+    uint4 *ring = smem_raw + (size_t)wib * (Cfg::smem_per_warp / 16);
+    StageMeta *meta = reinterpret_cast<StageMeta *>(smem_raw + (Cfg::smem_per_block / 16)) + wib * D;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_scan = 0, c_gather = 0, c_own = 0, c_write = 0;
     MarkTally mt;
-    if (lane < D) mbar_init(bar + lane, 1);
-    fence_proxy_async();   // the initialised barriers, to the copy engine
-    __syncwarp();
-    uint32_t phase = 0;    // bit s: parity of the phase of stage s waited for next
-    bool stuck = false;
 
     // ---- producer state (warp-uniform) ----
     int64_t p_it = warp - nwarps, p_e = 0, p_end = 0;
@@ -866,66 +784,57 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_bulk(Plan p)
         }
     };
     next_item();
+    // targets of the next stage to issue, loaded one stage ahead
     int32_t t_next = (p_it < total && p_e + lane < p_end) ? __ldg(p.tgt + p_e + lane) : -1;
 
     auto produce = [&](int slot) {
-        uint8_t *buf = ring + (size_t)slot * 32 * Cfg::W;
+        uint4 *buf = ring + (size_t)slot * 32 * LANES;
         if (p_it >= total) {
-            if (lane == 0) {
-                meta[slot].item = -1;
-                meta[slot].valid = 0u;
-                meta[slot].last = 0;
-                mbar_arrive_tx(bar + slot, 0u);
-            }
-            __syncwarp();
+            if (lane == 0) meta[slot].item = -1;
+            cp_async_commit();
             return;
         }
         int32_t w = t_next;
         const int64_t it = p_it;
         const bool last = p_e + 32 >= p_end;
+        // advance the producer and prefetch the following stage's targets
         p_e += 32;
         if (last) next_item();
         t_next = (p_it < total && p_e + lane < p_end) ? __ldg(p.tgt + p_e + lane) : -1;
         if (w >= 0 && test && !test_bit(Fc, w)) w = -1;
         const unsigned live = __ballot_sync(kFull, w >= 0);
+        // lane (g, gl) copies the gl-th 16 bytes of rows g, g+GPW, ...
+#pragma unroll
+        for (int k = 0; k < LANES; ++k) {
+            const int r = g + GPW * k;
+            const int32_t wr = __shfl_sync(kFull, w, r);
+            const uint8_t *src = wr >= 0 ? rc + (int64_t)wr * Cfg::W + gl * 16 : rc;
+            cp_async16(buf + r * LANES + gl, src, wr >= 0);
+        }
+        cp_async_commit();
         if (lane == 0) {
             meta[slot].item = it;
-            meta[slot].valid = live;
+            meta[slot].valid = __popc(live);
             meta[slot].last = last ? 1 : 0;
-            mbar_arrive_tx(bar + slot, (unsigned)__popc(live) * Cfg::W);
         }
-        __syncwarp();
-        fence_proxy_async();   // the slot's previous rows were read by plain loads
-        if (w >= 0) bulk_copy(buf + lane * Cfg::W, rc + (int64_t)w * Cfg::W, Cfg::W, bar + slot);
-        __syncwarp();
     };
 
     Row<LANES, 1> acc;
     row_zero(acc);
     bool any = false;
-    auto wait_stage = [&](int slot) {
-        const unsigned par = (phase >> slot) & 1u;
-        int spins = 0;
-        while (!mbar_try_wait(bar + slot, par))
-            if (++spins >= kWaitLimit) {
-                stuck = true;
-                break;
-            }
-        phase ^= 1u << slot;
-    };
     auto consume = [&](int slot) -> bool {
-        wait_stage(slot);
+        cp_async_wait<D - 1>();
         __syncwarp();
         const StageMeta m = meta[slot];
-        if (m.item < 0) return false;
-        const uint4 *buf = reinterpret_cast<const uint4 *>(ring + (size_t)slot * 32 * Cfg::W);
-#pragma unroll
-        for (int k = 0; k < LANES; ++k) {
-            const int r = g + GPW * k;
-            if ((m.valid >> r) & 1u) acc.v[0] = vmax4(acc.v[0], buf[r * LANES + gl]);
+        if (m.item < 0) {
+            __syncwarp();
+            return false;
         }
+        const uint4 *buf = ring + (size_t)slot * 32 * LANES;
+#pragma unroll
+        for (int k = 0; k < LANES; ++k) acc.v[0] = vmax4(acc.v[0], buf[(g + GPW * k) * LANES + gl]);
         if (m.valid) any = true;
-        c_gather += (uint32_t)__popc(m.valid);
+        c_gather += m.valid;
         __syncwarp();
         if (m.last) {
             row_warp_max(acc);
@@ -946,20 +855,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_bulk(Plan p)
         return true;
     };
 
-    int k = 0;
 #pragma unroll
     for (int s = 0; s < D - 1; ++s) produce(s);
-    for (;; ++k) {
+    for (int k = 0;; ++k) {
         produce((k + D - 1) % D);
-        const bool more = consume(k % D);
-        if (stuck || (!more && p_it >= total)) break;
+        if (!consume(k % D) && p_it >= total) break;
     }
-    // the D-1 stages produced after the last one consumed hold no copies in a
-    // normal run; after a stuck wait, give their copies a bounded chance to land
-    for (int s = 1; s < D; ++s) wait_stage((k + s) % D);
-    __syncwarp();
-    if (lane < D && !stuck) mbar_inval(bar + lane);
-    if (stuck && lane == 0) p.ctl->err = HANF_ETIMEOUT;
+    cp_async_wait<0>();
     flush_counters(p, cur, mt, c_scan, lane == 0 ? c_gather : 0u, c_own, c_write);
 }
 
@@ -2694,8 +2596,10 @@ struct UnionKernels {
         }
         if constexpr (VPL == 1 && LANES <= 8) {
             if (p.warp_variant == 2) {
+                using Cfg = AsyncCfg<LANES>;
+                const size_t smem = Cfg::smem_per_block + sizeof(StageMeta) * Cfg::D * (kBlock / 32);
                 const int ablocks = (p.union_async_warps * 32 + kBlock - 1) / kBlock;
-                k_union_warp_bulk<LANES><<<ablocks, kBlock, BulkCfg<LANES>::smem_per_block, s>>>(p);
+                k_union_warp_async<LANES><<<ablocks, kBlock, smem, s>>>(p);
             } else {
                 k_union_warp<LANES, VPL><<<blocks, kBlock, 0, s>>>(p);
             }
@@ -2760,11 +2664,12 @@ struct UnionKernels {
     static int async_occupancy()
     {
         if constexpr (VPL == 1 && LANES <= 8) {
-            const size_t smem = BulkCfg<LANES>::smem_per_block;
-            cudaFuncSetAttribute(k_union_warp_bulk<LANES>,
+            using Cfg = AsyncCfg<LANES>;
+            const size_t smem = Cfg::smem_per_block + sizeof(StageMeta) * Cfg::D * (kBlock / 32);
+            cudaFuncSetAttribute(k_union_warp_async<LANES>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int nb = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_union_warp_bulk<LANES>, kBlock,
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_union_warp_async<LANES>, kBlock,
                                                           smem);
             return nb;
         } else {
