@@ -459,6 +459,9 @@ def main():
                     help="register layout: one byte each, or five bit-planes")
     ap.add_argument("--autotune", action="store_true",
                     help="pick degree split and gather variant with hanf_autotune first")
+    ap.add_argument("--l2-hot-mb", type=int, default=0,
+                    help="persisting-L2 window over the hottest counter rows, MiB (0 = library "
+                         "default, negative = off)")
     ap.add_argument("--profile-steps", type=int, default=2,
                     help="runs of the profiled context that give the union-kernel time")
     args = ap.parse_args()
@@ -512,7 +515,7 @@ def main():
         tuned["layout"] = args.layout
         print(json.dumps({"autotune": tuned, "best_ms": tune_ms,
                           "tuning_s": time.perf_counter() - t_tune}), file=sys.stderr)
-    kw = dict(scatter_den=args.scatter_den)
+    kw = dict(scatter_den=args.scatter_den, l2_hot_bytes=args.l2_hot_mb << 20)
     kw.update(tuned)          # the tuner's choices, where it made one
     h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
                  use_graph=args.driver == "graph", **kw)
@@ -639,6 +642,7 @@ def main():
                        "scatter_den": args.scatter_den or "default",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (no flush)", "tuned": tuned,
+                       "l2_hot_mb": args.l2_hot_mb or "default",
                        "graph_gen_s": round(t_gen, 2)},
             "T": T_list[-1], "passes_per_step": passes_list[-1],
             "stats": {k: float(v) for k, v in stat.items()},

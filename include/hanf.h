@@ -121,9 +121,12 @@ typedef struct hanf_opts {
                               counter rows (stored first, by in-degree class)
                               of the buffer a pass reads in the L2's
                               persisting set-aside (an access-policy window on
-                              the union launches; the context's persisting-L2
-                              limit is raised for the context's lifetime and
-                              restored by hanf_destroy); 0 = off            */
+                              the pass's launches; the context's
+                              persisting-L2 limit is raised for the context's
+                              lifetime and restored by hanf_destroy, so two
+                              such contexts alive at once share it); 0 = 64
+                              MiB when the counters take 1 GiB or more, else
+                              off; negative = off (served jobs: off)       */
 } hanf_opts;
 
 /* Fill *opts with the defaults above. */

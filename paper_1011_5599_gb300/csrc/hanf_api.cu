@@ -260,6 +260,7 @@ struct hanf_ctx {
     const int32_t *perm;         // input id -> stored row (relabelled), or null
     uint8_t *stage;              // staging rows for relabelled register reads
     size_t l2_window;            // bytes of hot rows kept persisting in L2 (0 = off)
+    int graph_passes;            // passes in one iteration of the graph's loop body
     size_t l2_limit_before;      // the context's persisting-L2 limit before create
 };
 
@@ -296,7 +297,7 @@ int reset(hanf_ctx *c, int32_t max_t)
 
 // Access-policy window over the hottest rows of the buffer the coming pass
 // reads (stored first), or none (bytes = 0).
-int set_l2_window(hanf_ctx *c, const void *base, size_t bytes)
+int set_l2_window(hanf_ctx *c, cudaStream_t stream, const void *base, size_t bytes)
 {
     cudaStreamAttrValue v;
     std::memset(&v, 0, sizeof v);
@@ -305,7 +306,7 @@ int set_l2_window(hanf_ctx *c, const void *base, size_t bytes)
     v.accessPolicyWindow.hitRatio = bytes ? 1.0f : 0.0f;
     v.accessPolicyWindow.hitProp = bytes ? cudaAccessPropertyPersisting : cudaAccessPropertyNormal;
     v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    CU(cudaStreamSetAttribute(c->stream, cudaStreamAttributeAccessPolicyWindow, &v));
+    CU(cudaStreamSetAttribute(stream, cudaStreamAttributeAccessPolicyWindow, &v));
     if (c->fork.side)
         CU(cudaStreamSetAttribute(c->fork.side, cudaStreamAttributeAccessPolicyWindow, &v));
     return HANF_OK;
@@ -317,13 +318,13 @@ int one_pass(hanf_ctx *c)
     const DevCtl before = c->host_ctl;
     int nl = 0;
     if (c->l2_window) {
-        const int rc = set_l2_window(c, c->plan.regs[c->host_ctl.parity], c->l2_window);
+        const int rc = set_l2_window(c, c->stream, c->plan.regs[c->host_ctl.parity], c->l2_window);
         if (rc) return rc;
     }
     const cudaError_t le = hanf::launch_pass(c->plan, c->stream, 0, 0, prof ? c->ev[0] : nullptr,
                                              prof ? c->ev[1] : nullptr, &nl, &c->fork);
     if (c->l2_window) {
-        const int rc = set_l2_window(c, nullptr, 0);
+        const int rc = set_l2_window(c, c->stream, nullptr, 0);
         if (rc) return rc;
     }
     CU(le);
@@ -367,8 +368,24 @@ int build_graph(hanf_ctx *c)
     CU(cudaStreamBeginCaptureToGraph(c->capture_stream, body, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeThreadLocal));
     int nl = 0;
-    cudaError_t le = hanf::launch_pass(c->plan, c->capture_stream, h, 1, nullptr, nullptr, &nl,
+    cudaError_t le = cudaSuccess;
+    if (c->l2_window) {
+        // two passes a loop iteration, each with the window over the hot rows
+        // of the buffer it reads (a run starts at t = 0, reading regs[0])
+        for (int q = 0; q < 2 && le == cudaSuccess; ++q) {
+            if (set_l2_window(c, c->capture_stream, c->plan.regs[q], c->l2_window) != HANF_OK)
+                le = cudaErrorUnknown;
+            else
+                le = hanf::launch_pass(c->plan, c->capture_stream, h, 1, nullptr, nullptr, &nl,
                                        &c->fork);
+        }
+        if (le == cudaSuccess && set_l2_window(c, c->capture_stream, nullptr, 0) != HANF_OK)
+            le = cudaErrorUnknown;
+        c->graph_passes = 2;
+    } else {
+        le = hanf::launch_pass(c->plan, c->capture_stream, h, 1, nullptr, nullptr, &nl, &c->fork);
+        c->graph_passes = 1;
+    }
     cudaGraph_t captured = nullptr;
     cudaError_t ee = cudaStreamEndCapture(c->capture_stream, &captured);
     if (le != cudaSuccess || ee != cudaSuccess) {
@@ -695,7 +712,14 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
                           ? 3
                           : 0;
 
-    if (o.l2_hot_bytes > 0 && s.layout == 0) {
+    // persisting-L2 window: explicit size, or by default 64 MiB for counter
+    // arrays of 1 GiB and more (measured best on R-MAT 27, m = 64)
+    const int64_t l2_want = o.l2_hot_bytes != 0
+                                ? o.l2_hot_bytes
+                                : ((int64_t)std::max<int64_t>(n, 1) * s.W >= (int64_t(1) << 30)
+                                       ? int64_t(64) << 20
+                                       : 0);
+    if (l2_want > 0 && s.layout == 0) {
         // persisting L2 lines for the hottest counter rows (host-loop driver)
         int max_persist = 0, max_window = 0;
         size_t before = 0;
@@ -705,7 +729,7 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
                 cudaSuccess ||
             cudaDeviceGetLimit(&before, cudaLimitPersistingL2CacheSize) != cudaSuccess)
             return bail(fail(HANF_ECUDA, "L2 persistence queries failed"));
-        const size_t want = std::min<size_t>({(size_t)o.l2_hot_bytes, (size_t)max_persist,
+        const size_t want = std::min<size_t>({(size_t)l2_want, (size_t)max_persist,
                                               (size_t)max_window, (size_t)std::max<int64_t>(n, 1) * s.W});
         if (want > 0) {
             if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, std::max(want, before)) != cudaSuccess)
@@ -806,7 +830,8 @@ int drive(hanf_ctx *c, double *N_out, int32_t cap, int32_t *T_out, int32_t max_i
         CU(cudaGraphLaunch(c->gexec, c->stream));
         rc = read_ctl(c);
         if (rc) return rc;
-        c->launches += (int64_t)c->host_ctl.passes * pass_launch_count(c);
+        const int64_t gp = std::max(c->graph_passes, 1);
+        c->launches += (((int64_t)c->host_ctl.passes + gp - 1) / gp) * gp * pass_launch_count(c);
     } else {
         for (;;) {
             rc = one_pass(c);

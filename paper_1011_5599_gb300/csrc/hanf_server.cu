@@ -138,6 +138,7 @@ hanf_opts job_opts(const hanf_server *s, const hanf_job &j, cudaStream_t st)
     o.profile = 0;
     o.seeds = nullptr;
     o.stream = st;
+    o.l2_hot_bytes = -1;   // jobs share the GPU: no context-wide L2 set-aside
     return o;
 }
 
