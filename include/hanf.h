@@ -272,9 +272,13 @@ HANF_API int hanf_autotune(int64_t n, int64_t arcs, const int64_t *offsets,
  * order as soon as a worker is free and the job's workspace (as sized by
  * hanf_workspace_size) fits in the arena; the admitted job runs the whole of
  * Algorithm 2 as one CUDA graph on its worker's stream, so jobs of different
- * workers overlap on the GPU.  Every job has its own context: its result is
- * the same whether it runs alone or among others.  (The paper runs one graph
- * at a time; this layer is the serving pattern around its Algorithm 2.) */
+ * workers overlap on the GPU.  Small jobs (at most 65,536 nodes, default pass
+ * limit) admitted together with later queued small jobs of the same m, runs
+ * and graph placement share one context (num_graphs > 1, up to 64 jobs and
+ * 2^21 stored nodes), so they share launches too.  A job's result is the
+ * same whether it runs alone, batched or among others.  (The paper runs one
+ * graph at a time; this layer is the serving pattern around its Algorithm
+ * 2.) */
 typedef struct hanf_server hanf_server;
 
 typedef struct hanf_job {
@@ -315,7 +319,8 @@ HANF_API int hanf_server_wait(hanf_server *s, uint64_t id, int32_t timeout_ms, d
 HANF_API int hanf_server_cancel(hanf_server *s, uint64_t id);
 
 /* out = {jobs queued, jobs running, completed, failed, largest free arena
- * block, arena bytes}; nout <= 6. */
+ * block, arena bytes, contexts created (a batch of jobs counts once)};
+ * nout <= 7. */
 HANF_API int hanf_server_stats(hanf_server *s, double *out, int32_t nout);
 
 /* Stop the workers after their current jobs (queued jobs are cancelled) and

@@ -552,10 +552,10 @@ class Server:
         check(lib().hanf_server_cancel(self._srv, jid))
 
     def stats(self) -> dict:
-        out = np.zeros(6, dtype=np.float64)
-        check(lib().hanf_server_stats(self._srv, out.ctypes.data_as(ctypes.POINTER(_f64)), 6))
+        out = np.zeros(7, dtype=np.float64)
+        check(lib().hanf_server_stats(self._srv, out.ctypes.data_as(ctypes.POINTER(_f64)), 7))
         return dict(zip(("queued", "running", "completed", "failed", "largest_free",
-                         "arena_bytes"), out.tolist()))
+                         "arena_bytes", "contexts"), out.tolist()))
 
     def close(self):
         if getattr(self, "_srv", None):

@@ -102,3 +102,67 @@ def test_timeout_cancel_and_failure(H):
             srv.wait(d, timeout_ms=0)
         assert e.value.code == H.HANF_ETIMEOUT
         srv.wait(d)                                    # still completes afterwards
+
+
+def run_queued(H, jobs, on_device):
+    """Submit a long job, then `jobs` (graph, log2m, seed) while the only
+    worker is busy with it; returns each job's result or error code and the
+    server's statistics."""
+    import torch
+    with H.Server(1 << 28, workers=1) as srv:
+        big = G.rmat(15, seed=9)
+        first = srv.submit(big[0], big[1], 8, SEED)
+        ids = []
+        for (off, tgt), log2m, seed in jobs:
+            if on_device:
+                off, tgt = torch.from_numpy(off).cuda(), torch.from_numpy(tgt).cuda()
+            ids.append(srv.submit(off, tgt, log2m, seed, runs=2))
+        srv.wait(first)
+        results = []
+        for jid in ids:
+            try:
+                results.append(srv.wait(jid))
+            except H.HanfError as e:
+                results.append(e.code)
+        return results, srv.stats()
+
+
+def check_against_oracle(oracle, jobs, results):
+    for k, (((off, tgt), log2m, seed), res) in enumerate(zip(jobs, results)):
+        if isinstance(res, int):
+            continue
+        N, T, _ = res
+        for r in range(2):
+            No, To, _ = oracle.hyperanf(off, tgt, log2m, oracle.run_seed(seed, r))
+            assert T[r] == To, (k, r)
+            np.testing.assert_allclose(N[r], No, rtol=1e-12, atol=0)
+
+
+SMALL = [G.er(300 + 97 * i, 1200 + 300 * i, seed=40 + i) for i in range(10)] + \
+        [G.grid2d(9), G.path(70), G.empty(5), G.star(65)]
+BAD = (np.array([0, 2, 3], dtype=np.int64), np.array([0, 7, 1], dtype=np.int32))
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_small_jobs_share_contexts(H, oracle, on_device):
+    """Small queued jobs of one class (m, runs, graph placement) run in shared
+    contexts: fewer contexts than jobs, every result the oracle's; a bad graph
+    of another class fails on its own."""
+    jobs = [(g, 6, SEED + 3 * k) for k, g in enumerate(SMALL)]
+    jobs.insert(7, (BAD, 4, SEED))
+    results, st = run_queued(H, jobs, on_device)
+    assert results[7] == H.HANF_EINVAL
+    assert st["contexts"] <= 4, st          # the long job, a batch, the bad job
+    assert st["completed"] == len(jobs) and st["failed"] == 1
+    check_against_oracle(oracle, jobs, results)
+
+
+def test_bad_graph_in_a_batch_runs_everything_alone(H, oracle):
+    """A batch whose context fails (one graph invalid) puts its jobs back to
+    run alone: the bad job reports its own error, the others their results."""
+    jobs = [(g, 6, SEED + 3 * k) for k, g in enumerate(SMALL[:6])]
+    jobs.insert(3, (BAD, 6, SEED))
+    results, st = run_queued(H, jobs, False)
+    assert results[3] == H.HANF_EINVAL
+    assert all(not isinstance(r, int) for k, r in enumerate(results) if k != 3)
+    check_against_oracle(oracle, jobs, results)
