@@ -61,6 +61,7 @@ struct Job {
     int32_t status = 1;            // 1 queued, 2 running, 0 or <0 finished
     bool cancelled = false;
     bool alone = false;            // run in a context of its own (a batch failed)
+    int32_t outcome = 0;           // the run's status, published as `status` under the lock
     std::string error;
     std::vector<double> N;         // runs x (T+1)
     std::vector<int32_t> T;
@@ -311,7 +312,7 @@ bool run_batch(hanf_server *s, std::vector<std::shared_ptr<Job>> &jobs, const Ba
             std::copy(row, row + Tm + 1, job.N.begin() + (size_t)r * (Tm + 1));
         }
         job.T_max = Tm;
-        job.status = HANF_OK;
+        job.outcome = HANF_OK;
     }
     return true;
 }
@@ -344,7 +345,7 @@ void run_job(hanf_server *s, Job &job, uint8_t *ws, cudaStream_t st)
     } else {
         job.error = hanf_last_error();
     }
-    job.status = rc;
+    job.outcome = rc;
 }
 
 // The oldest queued job, and (if it is small) the later queued small jobs of
@@ -435,6 +436,7 @@ void worker_main(hanf_server *s, int w)
             } else {
                 for (auto &j : jobs) {
                     j->t_end = now;
+                    j->status = j->outcome;   // a waiter sees the result and its times together
                     if (j->status == HANF_OK) ++s->completed;
                     else ++s->failed;
                 }
