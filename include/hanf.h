@@ -192,6 +192,44 @@ HANF_API int hanf_registers(hanf_ctx *ctx, int32_t run, int64_t first, int64_t c
 HANF_API int hanf_digest(hanf_ctx *ctx, int32_t run, int64_t first, int64_t count,
                          uint64_t *digest_out);
 
+/* ---- One pass in steps: node-sharded runs ----------------------------------
+ * The distribution of Algorithm 2 over several GPUs that the paper's
+ * conclusion proposes (Pregel-style: every node computes its new counter from
+ * its successors' counters, then the changed counters are exchanged): shard q
+ * owns the input ids [lo_q, hi_q) and is a context over all n nodes whose CSR
+ * holds the arcs of its own nodes only (other rows empty), so a pass changes
+ * only its own counters.  One pass is
+ *   hanf_pass_begin   the pass flavour, marking and union kernels (no sync);
+ *   hanf_pass_collect its own changed nodes and their new rows, for sending;
+ *   hanf_pass_apply   the other shards' changed rows, received;
+ *   hanf_pass_end     stop decision and N(t+1), now over every changed node.
+ * Every shard then holds all counters of c_{t+1}, and N(t) (hanf_estimate),
+ * T and the changed counts are those of the unsharded run.  Byte layout and
+ * one graph only (HANF_ESTATE otherwise).  All buffers are device memory. */
+
+/* Start pass t -> t+1 (asynchronous).  *started_out = 0 if the run has
+ * already stabilised (nothing launched; then no other step may follow). */
+HANF_API int hanf_pass_begin(hanf_ctx *ctx, int32_t *started_out);
+
+/* The nodes with input ids in [first, first+count) that the open pass
+ * changed: their input ids into ids[] and their new rows (R*m bytes each,
+ * run-major, one byte per register; 16-byte aligned) into rows[], in no
+ * particular order, at most `cap` entries; *n_out (host) = how many there are.
+ * HANF_ERANGE if more than cap (call again with room for *n_out).
+ * Synchronises the stream. */
+HANF_API int hanf_pass_collect(hanf_ctx *ctx, int64_t first, int64_t count, int32_t *ids,
+                               uint8_t *rows, int64_t cap, int64_t *n_out);
+
+/* Counters other shards changed in the open pass: k input ids (each outside
+ * this shard's range, each once) and their new rows, as hanf_pass_collect
+ * returns them.  Asynchronous. */
+HANF_API int hanf_pass_apply(hanf_ctx *ctx, const int32_t *ids, const uint8_t *rows, int64_t k);
+
+/* Close the pass: *changed_out (host, nullable) = nodes changed in it, over
+ * all shards once every shard's rows were applied; 0 means stable.
+ * Synchronises the stream. */
+HANF_API int hanf_pass_end(hanf_ctx *ctx, int64_t *changed_out);
+
 /* Current pass index t (number of passes run since initialisation). */
 HANF_API int hanf_current_t(hanf_ctx *ctx, int32_t *t_out);
 

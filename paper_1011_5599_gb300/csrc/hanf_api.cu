@@ -261,6 +261,7 @@ struct hanf_ctx {
     uint8_t *stage;              // staging rows for relabelled register reads
     size_t l2_window;            // bytes of hot rows kept persisting in L2 (0 = off)
     int graph_passes;            // passes in one iteration of the graph's loop body
+    bool in_pass;                // between hanf_pass_begin and hanf_pass_end
     size_t l2_limit_before;      // the context's persisting-L2 limit before create
 };
 
@@ -759,6 +760,7 @@ int hanf_estimate(hanf_ctx *c, double *N_out)
 int hanf_iterate(hanf_ctx *c, int64_t *changed_out)
 {
     if (!c) return fail(HANF_EINVAL, "NULL context");
+    if (c->in_pass) return fail(HANF_ESTATE, "a stepped pass is open");
     int rc = read_ctl(c);
     if (rc) return rc;
     if (c->host_ctl.done) {
@@ -784,6 +786,7 @@ int hanf_run(hanf_ctx *c, int32_t max_iter, double *N_out, int32_t cap, int32_t 
 {
     if (!c || !N_out || !T_out) return fail(HANF_EINVAL, "NULL argument");
     if (cap < 1 || max_iter < 1) return fail(HANF_EINVAL, "cap and max_iter must be >= 1");
+    if (c->in_pass) return fail(HANF_ESTATE, "a stepped pass is open");
     const int32_t max_t = std::min<int32_t>(std::min(max_iter, cap), c->sz.history);
     int rc = reset(c, max_t);
     if (rc) return rc;
@@ -794,6 +797,7 @@ int hanf_continue(hanf_ctx *c, int32_t max_iter, double *N_out, int32_t cap, int
 {
     if (!c || !N_out || !T_out) return fail(HANF_EINVAL, "NULL argument");
     if (cap < 1 || max_iter < 1) return fail(HANF_EINVAL, "cap and max_iter must be >= 1");
+    if (c->in_pass) return fail(HANF_ESTATE, "a stepped pass is open");
     int rc = read_ctl(c);
     if (rc) return rc;
     DevCtl h = c->host_ctl;
@@ -916,6 +920,84 @@ int hanf_digest(hanf_ctx *c, int32_t run, int64_t first, int64_t count, uint64_t
     CU(cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     *digest_out = h;
+    return HANF_OK;
+}
+
+// ---- one pass in steps, for node-sharded runs ----
+
+int hanf_pass_begin(hanf_ctx *c, int32_t *started_out)
+{
+    if (!c || !started_out) return fail(HANF_EINVAL, "NULL argument");
+    if (c->in_pass) return fail(HANF_ESTATE, "a pass is already open");
+    if (c->plan.layout != 0 || c->plan.K != 1)
+        return fail(HANF_ESTATE, "stepped passes need the byte layout and one graph");
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    *started_out = 0;
+    if (c->host_ctl.done) return c->host_ctl.err ? ctl_fail(c->host_ctl.err) : HANF_OK;
+    if (c->l2_window) {
+        rc = set_l2_window(c, c->stream, c->plan.regs[c->host_ctl.parity], c->l2_window);
+        if (rc) return rc;
+    }
+    int nl = 0;
+    const cudaError_t le = hanf::launch_pass_union(c->plan, c->stream, nullptr, nullptr, &nl, &c->fork);
+    if (c->l2_window) {
+        rc = set_l2_window(c, c->stream, nullptr, 0);
+        if (rc) return rc;
+    }
+    CU(le);
+    c->launches += nl;
+    c->in_pass = true;
+    *started_out = 1;
+    return HANF_OK;
+}
+
+int hanf_pass_collect(hanf_ctx *c, int64_t first, int64_t count, int32_t *ids, uint8_t *rows,
+                      int64_t cap, int64_t *n_out)
+{
+    if (!c || !n_out || (cap > 0 && (!ids || !rows))) return fail(HANF_EINVAL, "NULL argument");
+    if (!c->in_pass) return fail(HANF_ESTATE, "no pass is open");
+    if (first < 0 || count < 0 || first + count > c->plan.n || cap < 0)
+        return fail(HANF_EINVAL, "node range out of bounds");
+    if ((reinterpret_cast<uintptr_t>(rows) & 15) != 0)
+        return fail(HANF_EINVAL, "rows must be 16-byte aligned");
+    unsigned long long *d = &c->plan.ctl->shard_count;
+    CU(cudaMemsetAsync(d, 0, sizeof *d, c->stream));
+    CU(hanf::launch_shard_collect(c->plan, first, count, ids, rows, cap, c->stream));
+    unsigned long long found = 0;
+    CU(cudaMemcpyAsync(&found, d, sizeof found, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->launches += 1;
+    *n_out = (int64_t)found;
+    if ((int64_t)found > cap)
+        return fail(HANF_ERANGE, "%lld changed nodes, room for %lld", (long long)found,
+                    (long long)cap);
+    return HANF_OK;
+}
+
+int hanf_pass_apply(hanf_ctx *c, const int32_t *ids, const uint8_t *rows, int64_t k)
+{
+    if (!c || (k > 0 && (!ids || !rows)) || k < 0) return fail(HANF_EINVAL, "bad argument");
+    if (!c->in_pass) return fail(HANF_ESTATE, "no pass is open");
+    if ((reinterpret_cast<uintptr_t>(rows) & 15) != 0)
+        return fail(HANF_EINVAL, "rows must be 16-byte aligned");
+    CU(hanf::launch_shard_apply(c->plan, c->perm, ids, rows, k, c->stream));
+    if (k > 0) c->launches += 1;
+    return HANF_OK;
+}
+
+int hanf_pass_end(hanf_ctx *c, int64_t *changed_out)
+{
+    if (!c) return fail(HANF_EINVAL, "NULL context");
+    if (!c->in_pass) return fail(HANF_ESTATE, "no pass is open");
+    c->in_pass = false;
+    int nl = 0;
+    CU(hanf::launch_pass_end(c->plan, c->stream, 0, 0, &nl));
+    c->launches += nl;
+    const int rc = read_ctl(c);
+    if (rc) return rc;
+    if (changed_out) *changed_out = (int64_t)c->host_ctl.last_changed;
+    if (c->host_ctl.err) return ctl_fail(c->host_ctl.err);
     return HANF_OK;
 }
 

@@ -34,6 +34,7 @@ struct DevCtl {
     // work counters since initialisation
     unsigned long long passes, push_passes, arcs_scanned, arcs_gathered, own_reads, writes;
     unsigned long long digest;               // result of the last hanf_digest
+    unsigned long long shard_count;          // rows found by the last shard collect
 };
 
 // Everything a kernel needs that does not change between passes.  Passed by
@@ -117,6 +118,21 @@ struct PassFork {
 cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
                         cudaEvent_t ev_union0, cudaEvent_t ev_union1, int *nlaunch,
                         const PassFork *fk = nullptr);
+// The two halves of launch_pass: the pass flavour, marking and union kernels;
+// then the stop decision (t, parity, T of each slot) and the estimate.  A
+// node-sharded run exchanges the changed counters between them.
+cudaError_t launch_pass_union(const Plan &p, cudaStream_t s, cudaEvent_t ev_union0,
+                              cudaEvent_t ev_union1, int *nlaunch, const PassFork *fk = nullptr);
+cudaError_t launch_pass_end(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h,
+                            int use_cond, int *nlaunch);
+// Node-sharded runs: the rows of the nodes a pass changed whose input id lies
+// in [first, first + count), compacted (input ids, rows) into caller buffers
+// of `cap` entries (ctl->shard_count counts them all); and the rows received
+// from other shards written into both counter buffers, marked changed.
+cudaError_t launch_shard_collect(const Plan &p, int64_t first, int64_t count, int32_t *ids,
+                                 uint8_t *rows, int64_t cap, cudaStream_t s);
+cudaError_t launch_shard_apply(const Plan &p, const int32_t *perm, const int32_t *ids,
+                               const uint8_t *rows, int64_t k, cudaStream_t s);
 int union_occupancy_warps(int W, int nsm);
 int small_async_blocks(int W);
 int scatter_occupancy_warps(int W, int nsm);

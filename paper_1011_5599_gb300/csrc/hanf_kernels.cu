@@ -2549,6 +2549,98 @@ __global__ void __launch_bounds__(kBlock) k_digest(Plan p, int32_t r, int64_t fi
     if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
+// ---------------------------------------------------------------- node-sharded runs
+
+// Node-sharded runs (the Pregel-style distribution of Algorithm 2 that the
+// paper's conclusion proposes): every shard keeps all n counters but holds the
+// arcs of its own nodes only, so a pass changes only its own nodes.  Between
+// the union kernels and the end of the pass, each shard's changed nodes (the
+// bitmap F_{t+1}, restricted to input ids [first, first + count)) and their
+// new rows are compacted for the exchange.  A warp per bitmap word; the order
+// of the entries depends on timing, which nothing downstream depends on.
+__global__ void __launch_bounds__(kBlock) k_shard_collect(Plan p, int64_t first, int64_t count,
+                                                          int32_t *ids, uint8_t *rows, int64_t cap)
+{
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    const int cur = c->parity;
+    const unsigned long long *Fn = p.F[cur ^ 1];
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.regs[cur ^ 1]);
+    uint4 *dst = reinterpret_cast<uint4 *>(rows);
+    const int vec = p.W >> 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < p.nwords; i += nwarps) {
+        const unsigned long long bits = Fn[i];
+        if (bits == 0ull) continue;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            const int64_t v = i * 64 + 32 * h + lane;
+            int32_t id = -1;
+            if ((bits >> (32 * h + lane)) & 1ull) {
+                id = p.orig_id ? __ldg(p.orig_id + v) : (int32_t)v;
+                if (id < first || id >= first + count) id = -1;
+            }
+            const unsigned bal = __ballot_sync(kFull, id >= 0);
+            if (bal == 0u) continue;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&p.ctl->shard_count, (unsigned long long)__popc(bal));
+            base = __shfl_sync(kFull, base, 0);
+            if (id >= 0) {
+                const unsigned long long slot = base + __popc(bal & ((1u << lane) - 1u));
+                if (slot < (unsigned long long)cap) {
+                    ids[slot] = id;
+                    for (int k = 0; k < vec; ++k) dst[(int64_t)slot * vec + k] = src[v * vec + k];
+                }
+            }
+        }
+    }
+}
+
+// The rows other shards changed in this pass: written into both counter
+// buffers (the current one is not read again in this pass, and the next
+// pass's target must already hold them, as this shard never visits these
+// nodes), marked in F_{t+1}, counted as changed nodes and per run (a run
+// counts when its registers differ from the row this shard held).  A warp
+// per entry.
+__global__ void __launch_bounds__(kBlock) k_shard_apply(Plan p, const int32_t *perm,
+                                                        const int32_t *ids, const uint8_t *rows,
+                                                        int64_t k)
+{
+    const DevCtl *c = p.ctl;
+    if (c->done) return;
+    const int cur = c->parity;
+    uint4 *rc = reinterpret_cast<uint4 *>(p.regs[cur]);
+    uint4 *rn = reinterpret_cast<uint4 *>(p.regs[cur ^ 1]);
+    const uint4 *src = reinterpret_cast<const uint4 *>(rows);
+    const int vec = p.W >> 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = warp; e < k; e += nwarps) {
+        const int32_t id = __ldg(ids + e);
+        if (id < 0 || (int64_t)id >= p.n) continue;   // checked by the host as well
+        const int64_t v = perm ? (int64_t)__ldg(perm + id) : (int64_t)id;
+        uint32_t mask = 0;
+        for (int j = lane; j < vec; j += 32) {
+            const uint4 nw = src[e * vec + j];
+            if (!veq(nw, rc[v * vec + j])) mask |= 1u << ((j << 4) >> p.b);
+            rn[v * vec + j] = nw;
+            rc[v * vec + j] = nw;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mask |= __shfl_xor_sync(kFull, mask, o);
+        if (lane == 0 && mask) {
+            const unsigned long long bit = 1ull << (v & 63);
+            if ((atomicOr(&p.F[cur ^ 1][v >> 6], bit) & bit) == 0ull)
+                atomicAdd(&p.ctl->changed_count[cur ^ 1], 1ull);
+            for (int r = 0; r < p.R; ++r)
+                if ((mask >> r) & 1u) atomicAdd(&p.slot_changed[r], 1ull);
+        }
+    }
+}
+
 template <typename F>
 cudaError_t with_planes(int m, F &&f)
 {
@@ -2820,6 +2912,14 @@ cudaError_t launch_est_changed(const Plan &p, cudaStream_t s)
 cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h, int use_cond,
                         cudaEvent_t ev0, cudaEvent_t ev1, int *nlaunch, const PassFork *fk)
 {
+    const cudaError_t err = launch_pass_union(p, s, ev0, ev1, nlaunch, fk);
+    if (err != cudaSuccess) return err;
+    return launch_pass_end(p, s, h, use_cond, nlaunch);
+}
+
+cudaError_t launch_pass_union(const Plan &p, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                              int *nlaunch, const PassFork *fk)
+{
     k_prep<<<1, 1, 0, s>>>(p);
     k_clear<<<grid_for(std::max<int64_t>(p.nwords, p.S), kBlock, 152 * 16), kBlock, 0, s>>>(p);
     if (p.in_off) k_mark<<<grid_for(p.nwords, kBlock / 32, 152 * 8), kBlock, 0, s>>>(p);
@@ -2846,13 +2946,19 @@ cudaError_t launch_pass(const Plan &p, cudaStream_t s, cudaGraphConditionalHandl
     }
     if (err != cudaSuccess) return err;
     if (ev1) cudaEventRecord(ev1, s);
+    if (nlaunch)
+        *nlaunch += 3 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (!p.layout && p.W <= 128 ? 1 : 0) +
+                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass_end(const Plan &p, cudaStream_t s, cudaGraphConditionalHandle h,
+                            int use_cond, int *nlaunch)
+{
     if (p.S > 8) k_slot_T<<<grid_for(p.S, kBlock, 152 * 4), kBlock, 0, s>>>(p);
     k_post<<<1, 1, 0, s>>>(p, h, use_cond);
-    if (nlaunch)
-        *nlaunch += 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
-                    (!p.layout && p.W <= 128 ? 1 : 0) +
-                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0);
-    err = cudaGetLastError();
+    if (nlaunch) *nlaunch += 2 + (p.S > 8 ? 1 : 0);
+    const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     return launch_estimate(p, s, nlaunch);
 }
@@ -2996,6 +3102,22 @@ cudaError_t launch_digest(const Plan &p, int32_t run, int64_t first, int64_t cou
 {
     if (count <= 0) return cudaSuccess;
     k_digest<<<grid_for(count, kBlock), kBlock, 0, s>>>(p, run, first, count, perm, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_collect(const Plan &p, int64_t first, int64_t count, int32_t *ids,
+                                 uint8_t *rows, int64_t cap, cudaStream_t s)
+{
+    k_shard_collect<<<grid_for(p.nwords, kBlock / 32, 152 * 8), kBlock, 0, s>>>(p, first, count, ids,
+                                                                                  rows, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_apply(const Plan &p, const int32_t *perm, const int32_t *ids,
+                               const uint8_t *rows, int64_t k, cudaStream_t s)
+{
+    if (k <= 0) return cudaSuccess;
+    k_shard_apply<<<grid_for(k, kBlock / 32, 152 * 8), kBlock, 0, s>>>(p, perm, ids, rows, k);
     return cudaGetLastError();
 }
 

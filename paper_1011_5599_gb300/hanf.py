@@ -22,7 +22,8 @@ FRONTIER = {"off": 0, "pull": 1, "auto": 2}
 
 # Every function declared in include/hanf.h.
 EXPORTS = ("hanf_default_opts", "hanf_workspace_size", "hanf_create", "hanf_estimate",
-           "hanf_iterate", "hanf_run", "hanf_registers", "hanf_digest", "hanf_current_t",
+           "hanf_iterate", "hanf_run", "hanf_registers", "hanf_digest", "hanf_pass_begin",
+           "hanf_pass_collect", "hanf_pass_apply", "hanf_pass_end", "hanf_current_t",
            "hanf_counters",
            "hanf_trace", "hanf_checkpoint_size", "hanf_checkpoint_save", "hanf_checkpoint_load",
            "hanf_continue", "hanf_node_stats", "hanf_node_radius", "hanf_stats",
@@ -101,6 +102,14 @@ def lib():
         L.hanf_registers.argtypes = [_vp, _i32, _i64, _i64, _vp]
         L.hanf_digest.restype = _i32
         L.hanf_digest.argtypes = [_vp, _i32, _i64, _i64, ctypes.POINTER(_u64)]
+        L.hanf_pass_begin.restype = _i32
+        L.hanf_pass_begin.argtypes = [_vp, ctypes.POINTER(_i32)]
+        L.hanf_pass_collect.restype = _i32
+        L.hanf_pass_collect.argtypes = [_vp, _i64, _i64, _vp, _vp, _i64, ctypes.POINTER(_i64)]
+        L.hanf_pass_apply.restype = _i32
+        L.hanf_pass_apply.argtypes = [_vp, _vp, _vp, _i64]
+        L.hanf_pass_end.restype = _i32
+        L.hanf_pass_end.argtypes = [_vp, ctypes.POINTER(_i64)]
         L.hanf_current_t.restype = _i32
         L.hanf_current_t.argtypes = [_vp, ctypes.POINTER(_i32)]
         L.hanf_counters.restype = _i32
@@ -153,6 +162,11 @@ def lib():
         L.hanf_last_error.argtypes = []
         _lib = L
         return L
+
+
+def torch_int32():
+    import torch
+    return torch.int32
 
 
 def check(rc: int):
@@ -422,6 +436,46 @@ class HyperANF:
         out = _u64()
         check(lib().hanf_digest(self._ctx, run, first, count, ctypes.byref(out)))
         return out.value
+
+    # -- one pass in steps (node-sharded runs) ------------------------------
+    def pass_begin(self) -> bool:
+        """hanf_pass_begin: False if the run is already stable."""
+        started = _i32()
+        check(lib().hanf_pass_begin(self._ctx, ctypes.byref(started)))
+        return bool(started.value)
+
+    def pass_collect(self, first: int, count: int, cap: int | None = None):
+        """hanf_pass_collect: (ids, rows) CUDA tensors of this range's changed
+        nodes, rows of R*m bytes."""
+        import torch
+        cap = 1024 if cap is None else cap
+        while True:
+            ids = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
+            rows = torch.empty((max(cap, 1), self.R * self.m), dtype=torch.uint8, device=self.device)
+            n = _i64()
+            rc = lib().hanf_pass_collect(self._ctx, first, count, ids.data_ptr(), rows.data_ptr(),
+                                         cap, ctypes.byref(n))
+            if rc == HANF_ERANGE and n.value > cap:
+                cap = n.value
+                continue
+            check(rc)
+            return ids[:n.value], rows[:n.value]
+
+    def pass_apply(self, ids, rows) -> None:
+        """hanf_pass_apply of CUDA tensors (int32 ids, uint8 rows)."""
+        k = int(ids.numel())
+        ids = ids.to(device=self.device, dtype=torch_int32()).contiguous()
+        rows = rows.to(device=self.device).contiguous()
+        check(lib().hanf_pass_apply(self._ctx, ids.data_ptr() if k else None,
+                                    rows.data_ptr() if k else None, k))
+        self._keep_apply = (ids, rows)     # alive until the stream has used them
+
+    def pass_end(self) -> int:
+        """hanf_pass_end: nodes changed in the pass, over all shards."""
+        ch = _i64()
+        check(lib().hanf_pass_end(self._ctx, ctypes.byref(ch)))
+        self._keep_apply = None
+        return ch.value
 
     @property
     def t(self) -> int:
