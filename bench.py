@@ -430,6 +430,84 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------ one graph across ranks
+
+def run_sharded(args):
+    """One graph over the ranks: contiguous node shards balanced by arcs, every
+    rank holding all counters and its own arcs, changed counters all-gathered
+    after each pass (NCCL).  value = all ranks' gathered merges / the slowest
+    rank's time per step; the same graph on every N (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1011_5599_gb300 import build as B
+    from paper_1011_5599_gb300 import sharded
+    B.build()
+    from paper_1011_5599_gb300.hanf import HyperANF
+    from paper_1011_5599_gb300.replicas import reduce_max_sum
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    device = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(device)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    wl = WORKLOADS[args.workload]
+    log2m, R = wl["log2m"], wl["runs"]
+    m = 1 << log2m
+    off, tgt = make_graph(wl, args.seed, device)            # the same graph on every rank
+    n, arcs = off.numel() - 1, tgt.numel()
+    ranges = sharded.partition(off, world)
+    lo, hi = ranges[rank]
+    loff, ltgt = sharded.local_csr(off, tgt, lo, hi)
+    del off, tgt
+    torch.cuda.empty_cache()
+    exchange = sharded.group_exchange if world > 1 else sharded.local_exchange
+
+    def step():
+        with HyperANF(loff, ltgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
+                      l2_hot_bytes=args.l2_hot_mb << 20) as h:
+            N, T = sharded.run([h], [(lo, hi)], exchange=exchange)
+            c = h.counters()
+        return N, T, c
+
+    for _ in range(args.warmup):
+        step()
+    gathered, launches = 0.0, 0
+    with ClockSampler(gpu_index_for(device)) as clocks:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            N, T, c = step()
+            gathered += c["arcs_gathered"] * m * R
+            launches += int(c["launches"])
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        elapsed = time.perf_counter() - t0
+    step_all, gathered_all = reduce_max_sum(elapsed / args.steps, gathered / args.steps,
+                                            device=device)
+    line = {"metric": METRIC, "value": gathered_all / step_all, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_all,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "metric_definition": "(successor counters gathered) x m x R per step, all ranks / "
+                                 "slowest rank's step time (context creation, stepped passes "
+                                 "and the exchange included)",
+            "config": {"workload": wl["text"], "n": n, "arcs": arcs, "m": m, "runs": R,
+                       "parallelism": f"node shards x{world}", "shard_arcs": int(ltgt.numel()),
+                       "l2": "inputs larger than L2 (no flush)"},
+            "T": int(T), "N_T": float(N[-1][0]), "gpu_launches": launches,
+            "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 # ------------------------------------------------------------------ CUDA arm
 
 def main():
@@ -459,6 +537,9 @@ def main():
                     help="register layout: one byte each, or five bit-planes")
     ap.add_argument("--autotune", action="store_true",
                     help="pick degree split and gather variant with hanf_autotune first")
+    ap.add_argument("--sharded", action="store_true",
+                    help="one graph across the ranks (node shards exchanging changed counters "
+                         "every pass; strong scaling) instead of one replica per rank")
     ap.add_argument("--l2-hot-mb", type=int, default=0,
                     help="persisting-L2 window over the hottest counter rows, MiB (0 = library "
                          "default, negative = off)")
@@ -471,6 +552,8 @@ def main():
         return run_serve(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.sharded:
+        return run_sharded(args)
 
     import numpy as np
     import torch
