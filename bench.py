@@ -58,6 +58,8 @@ WORKLOADS = {
     "web20": dict(kind="web", n=1 << 20, log2m=6, runs=8,
                   text="web-like n=2^20 (power-law out-degree 2.1, mean 16, host blocks), "
                        "m=64, R=8 runs batched"),
+    "web18": dict(kind="web", n=1 << 18, log2m=6, runs=8,
+                  text="web-like n=2^18, m=64, R=8 runs batched (profiling case)"),
     "er": dict(kind="er", n=10000, arcs=50000, log2m=4, runs=1,
                text="directed ER n=10^4, 5*10^4 arcs, m=16, 1 run"),
 }
@@ -68,6 +70,7 @@ CPU_SAMPLE = {"rmat27": dict(kind="rmat", scale=22, ef=16, sym=False),
               "rmat24sym": dict(kind="rmat", scale=18, ef=16, sym=True),
               "rmat23sym": dict(kind="rmat", scale=17, ef=16, sym=True),
               "web20": dict(kind="web", n=1 << 16),
+              "web18": dict(kind="web", n=1 << 14),
               "er": dict(kind="er", n=10000, arcs=50000)}
 
 
