@@ -157,10 +157,10 @@ def gpu_index_for(device):
 # ------------------------------------------------------------------ profile summary
 
 def ncu_traffic(workload, layout="byte"):
-    """Per-launch DRAM bytes of one pass's union launches from the committed
-    ncu record of this workload and register layout (profiles/traffic.json),
-    or None when there is none or the kernel source changed since the
-    capture."""
+    """DRAM bytes of a dense pass's union launches (the launch the roofline
+    reports) from the committed ncu record of this workload and register
+    layout (profiles/traffic.json), or None when there is none or the kernel
+    source changed since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -637,12 +637,18 @@ def main():
                   profile=True, **kw)
     hp.run()
     prof_ms, prof_bytes, prof_gathered, rows = 0.0, 0.0, 0, []
+    dense_ms, dense_bytes, dense_n = 0.0, 0.0, 0
     for _ in range(max(args.profile_steps, 1)):
         hp.run()
         rows = hp.trace()
         prof_ms += sum(r["union_ms"] for r in rows)
         prof_bytes += sum(union_bytes(r, n, row_bytes) for r in rows)
         prof_gathered += hp.counters()["arcs_gathered"] * m * R
+        for r in rows:
+            if int(r["mode"]) == 2:          # dense pull passes: the dominant launches
+                dense_ms += r["union_ms"]
+                dense_bytes += union_bytes(r, n, row_bytes)
+                dense_n += 1
     psteps = max(args.profile_steps, 1)
     if prof_gathered != psteps * gathered / args.steps:
         raise RuntimeError("the profiled run gathered a different number of counters")
@@ -707,14 +713,22 @@ def main():
                "sample": f"{desc}; {secs:.1f} s"}
 
     peak, peak_kind = measured_peak()
-    achieved = bytes_per_launch / (union_launch_ms / 1e3) / 1e9 if union_launch_ms > 0 else None
+    all_gbs = bytes_per_launch / (union_launch_ms / 1e3) / 1e9 if union_launch_ms > 0 else None
+    if dense_n:
+        launch_bytes, launch_ms = dense_bytes / dense_n, dense_ms / dense_n
+        kernel = "union launches of a dense pull pass (k_union_small_async, k_union_warp, ...)"
+    else:
+        launch_bytes, launch_ms = bytes_per_launch, union_launch_ms
+        kernel = "union launches of one pass (k_union_*, k_scatter*, k_hub_finish)"
+    achieved = launch_bytes / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else None
     traffic = ncu_traffic(args.workload, args.layout)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic, "peak_kind": peak_kind,
-            "kernel": "union launches of one pass (k_union_*, k_scatter*, k_hub_finish)",
-            "algorithmic_bytes_per_launch": bytes_per_launch,
-            "avg_launch_ms": union_launch_ms}
+            "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
+            "algorithmic_bytes_per_launch": launch_bytes, "avg_launch_ms": launch_ms,
+            "all_passes": {"algorithmic_bytes_per_launch": bytes_per_launch,
+                           "avg_launch_ms": union_launch_ms, "achieved": all_gbs,
+                           "frac": (all_gbs / peak) if all_gbs else None}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * step_all, "higher_is_better": True,
