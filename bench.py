@@ -532,7 +532,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--trace", action="store_true", help="per-pass trace of one run on stderr")
-    ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2, 3])
+    ap.add_argument("--gather-variant", type=int, default=0, choices=[0, 1, 2, 3, 4])
+    ap.add_argument("--dense-den", type=int, default=0,
+                    help="dense pull passes while the changed nodes' in-arcs are at least "
+                         "arcs/dense_den (0 = library default)")
     ap.add_argument("--scatter-den", type=int, default=0,
                     help="pure-push passes below arcs/scatter_den changed in-arcs (0 = library "
                          "default, negative = never)")
@@ -601,7 +604,8 @@ def main():
         tuned["layout"] = args.layout
         print(json.dumps({"autotune": tuned, "best_ms": tune_ms,
                           "tuning_s": time.perf_counter() - t_tune}), file=sys.stderr)
-    kw = dict(scatter_den=args.scatter_den, l2_hot_bytes=args.l2_hot_mb << 20)
+    kw = dict(scatter_den=args.scatter_den, dense_den=args.dense_den,
+              l2_hot_bytes=args.l2_hot_mb << 20)
     kw.update(tuned)          # the tuner's choices, where it made one
     h = HyperANF(off, tgt, log2m, 0x5EED, runs=R, frontier="auto", device=device,
                  use_graph=args.driver == "graph", **kw)
@@ -740,6 +744,7 @@ def main():
             "config": {"workload": wl["text"], "n": n, "arcs": arcs, "m": m, "runs": R,
                        "layout": args.layout, "frontier": "auto", "driver": args.driver,
                        "scatter_den": args.scatter_den or "default",
+                       "dense_den": args.dense_den or "default",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (no flush)", "tuned": tuned,
                        "l2_hot_mb": args.l2_hot_mb or "default",

@@ -92,9 +92,9 @@ typedef struct hanf_opts {
                               shared-memory ring for medium-degree nodes and
                               hub segments; 3 = asynchronous copies into
                               per-lane shared-memory slots in the small-degree
-                              kernel's dense passes; 0 = the default, 3 for
-                              rows of at most 128 bytes (2 and 3 apply to such
-                              rows only), 1 otherwise                         */
+                              kernel's dense passes; 4 = both 2 and 3; 0 = the
+                              default, 3 for rows of at most 128 bytes (2, 3
+                              and 4 apply to such rows only), 1 otherwise     */
     int32_t layout;        /* 0 = one byte per register; 1 = five bit-planes of
                               m bits (5m/8 bytes per counter; runs = 1 and
                               m >= 32); results are identical               */

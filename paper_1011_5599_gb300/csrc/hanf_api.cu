@@ -103,7 +103,7 @@ int make_sizes(int64_t n, int64_t arcs, int32_t log2m, const hanf_opts &o, int32
         return fail(HANF_EINVAL, "frontier=%d invalid", o.frontier);
     if (o.push_den < 1) return fail(HANF_EINVAL, "push_den=%d < 1", o.push_den);
     if (o.dense_den < 0) return fail(HANF_EINVAL, "dense_den=%d < 0", o.dense_den);
-    if (o.gather_variant < 0 || o.gather_variant > 3)
+    if (o.gather_variant < 0 || o.gather_variant > 4)
         return fail(HANF_EINVAL, "gather_variant=%d invalid", o.gather_variant);
     if (o.small_max_deg < 0 || o.hub_min_deg < 0 || o.history_cap < 0)
         return fail(HANF_EINVAL, "negative tuning option");
@@ -705,10 +705,10 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
                              : hanf::union_occupancy_warps(s.W, c->nsm);
     p.scatter_warps = s.layout ? 0 : hanf::scatter_occupancy_warps(s.W, c->nsm);
     p.union_async_warps = s.layout ? 0 : hanf::union_async_warps(s.W, c->nsm);
-    p.warp_variant = (o.gather_variant == 2 && p.union_async_warps > 0) ? 2 : 1;
+    p.warp_variant = ((o.gather_variant == 2 || o.gather_variant == 4) && p.union_async_warps > 0) ? 2 : 1;
     // asynchronous copies in the small-degree kernel by default (rows of at
     // most 128 bytes; measured 26.4 -> 25.1 ms a dense R-MAT 27 pass)
-    p.small_variant = ((o.gather_variant == 0 || o.gather_variant == 3) && !s.layout &&
+    p.small_variant = ((o.gather_variant == 0 || o.gather_variant >= 3) && !s.layout &&
                        s.W <= 128 && hanf::small_async_blocks(s.W) > 0)
                           ? 3
                           : 0;

@@ -207,14 +207,26 @@ def test_relabelled_registers_by_input_id(H, oracle):
                 assert np.array_equal(h.registers(r, first, count), full[r][first:first + count])
 
 
+@pytest.mark.parametrize("variant", [2, 4])
 @pytest.mark.parametrize("log2m", [4, 5, 6, 7, 8])
-def test_async_gather_variant(H, oracle, log2m):
-    """The asynchronous-copy gathers give the same results (rows up to 128 B;
-    wider rows fall back to register batches)."""
+def test_async_gather_variant(H, oracle, log2m, variant):
+    """The asynchronous-copy gathers of the medium-degree and hub kernel (2),
+    also with those of the small-degree kernel (4), give the same results
+    (rows up to 128 B; wider rows fall back to register batches)."""
     off, tgt = G.rmat(13, seed=10)
-    for frontier in ("pull", "auto"):
-        check_run(H, oracle, off, tgt, log2m, frontier=frontier, gather_variant=2,
+    for frontier in ("off", "pull", "auto"):
+        check_run(H, oracle, off, tgt, log2m, frontier=frontier, gather_variant=variant,
                   small_max_deg=4, hub_min_deg=256)
+    if log2m <= 6:
+        # two runs share a row of up to 128 bytes; node degrees straddle the
+        # 32-arc stages (31, 32, 33 arcs) and hub segments end mid-stage
+        check_run(H, oracle, off, tgt, log2m, R=2, frontier="auto", gather_variant=variant,
+                  small_max_deg=31, hub_min_deg=97)
+        # many more warps than work items; a web-like graph; an R-MAT graph
+        # with arc-less nodes
+        for g in (G.star(300), G.web(1 << 12, seed=7), G.rmat(12, seed=8)):
+            check_run(H, oracle, *g, log2m, frontier="auto", gather_variant=variant,
+                      small_max_deg=8, hub_min_deg=64)
 
 
 @pytest.mark.parametrize("log2m", [4, 5, 6, 7])

@@ -109,14 +109,16 @@ def run_queued(H, jobs, on_device):
     worker is busy with it; returns each job's result or error code and the
     server's statistics."""
     import torch
+    if on_device:
+        jobs = [((torch.from_numpy(off).cuda(), torch.from_numpy(tgt).cuda()), log2m, seed)
+                for (off, tgt), log2m, seed in jobs]
+        torch.cuda.synchronize()
     with H.Server(1 << 28, workers=1) as srv:
-        big = G.rmat(15, seed=9)
-        first = srv.submit(big[0], big[1], 8, SEED)
-        ids = []
-        for (off, tgt), log2m, seed in jobs:
-            if on_device:
-                off, tgt = torch.from_numpy(off).cuda(), torch.from_numpy(tgt).cuda()
-            ids.append(srv.submit(off, tgt, log2m, seed, runs=2))
+        # a directed path of 3,000 nodes stabilises after 2,999 passes: the
+        # worker stays busy with it while every other job is queued
+        long_off, long_tgt = G.path(3000)
+        first = srv.submit(long_off, long_tgt, 8, SEED)
+        ids = [srv.submit(off, tgt, log2m, seed, runs=2) for (off, tgt), log2m, seed in jobs]
         srv.wait(first)
         results = []
         for jid in ids:
