@@ -81,9 +81,11 @@ typedef struct hanf_opts {
                               device-side while node (no host syncs)           */
     int32_t profile;       /* 1 = time the union kernels of every pass with
                               CUDA events and keep a per-pass trace           */
-    int32_t dense_den;     /* while at least n/dense_den counters changed, a
-                              pull pass gathers every successor without
-                              testing the changed bitmap; 0 = 2               */
+    int32_t dense_den;     /* while the changed counters' in-arcs are at least
+                              arcs/dense_den, a pull pass gathers every
+                              successor without testing the changed bitmap;
+                              0 = the default: arcs/2, or 15 arcs/16 for rows
+                              of 512 bytes and more                           */
     int32_t relabel;       /* 1 = store the counters in decreasing in-degree
                               order (hot counters share cache lines); results
                               and hanf_registers use input ids either way    */

@@ -519,7 +519,13 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.nwords = s.nwords;
     p.frontier = o.frontier;
     p.push_den = o.push_den;
-    p.dense_den = o.dense_den ? o.dense_den : 2;
+    // dense pulls while changed in-arcs >= arcs * dense_num / dense_den.  The
+    // per-arc bitmap test pays off sooner with wide rows: with 512-byte rows
+    // (web-like graph, 8 runs) a tested pass beat a dense one below about 92%
+    // of the successors changed, while with 64- and 128-byte rows it was
+    // slower even at 82% (R-MAT 27 pass 4: 34 against 23 ms)
+    p.dense_num = o.dense_den ? 1 : (p.W >= 512 ? 15 : 1);
+    p.dense_den = o.dense_den ? o.dense_den : (p.W >= 512 ? 16 : 2);
     // scatter passes by default for rows of at most 128 bytes: with wider rows a
     // pushed pair costs a whole row of compare-and-swaps and the systolic pull
     // measured faster (web-like graph, 512-byte rows)

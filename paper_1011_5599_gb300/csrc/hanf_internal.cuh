@@ -93,7 +93,7 @@ struct Plan {
     int32_t *ns_rad;                  // first t with E_v(t) >= ns_alpha E_v(T)
     double ns_alpha;
     int32_t node_stats, ns_radius_mode;
-    int32_t frontier, push_den, dense_den, scatter_den;
+    int32_t frontier, push_den, dense_num, dense_den, scatter_den;
     int32_t scatter_seg;              // scatter passes: in-arcs per segment, and the
     int32_t scatter_inline;           // in-degree above which a list is segmented
     int32_t history_cap;

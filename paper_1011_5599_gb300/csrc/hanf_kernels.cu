@@ -1048,8 +1048,8 @@ __global__ void k_prep(Plan p)
     else if (p.frontier == HANF_FRONTIER_AUTO && p.in_off != nullptr && changed * p.push_den < p.n)
         mode = kModePush;
     else if (p.in_off != nullptr
-                 ? (long long)c->changed_in_arcs * p.dense_den >= p.arcs
-                 : changed * p.dense_den >= p.n)
+                 ? (long long)c->changed_in_arcs * p.dense_den >= p.arcs * p.dense_num
+                 : changed * p.dense_den >= p.n * p.dense_num)
         mode = kModeDense;   // most successors changed: skip the per-arc test
     c->mode = mode;
     c->changed_count[c->parity ^ 1] = 0;
@@ -1107,22 +1107,30 @@ __global__ void k_mark(Plan p)
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < p.nwords; i += nwarps) {
-        unsigned long long bits = Fc[i];
-        while (bits) {
-            const int32_t w = (int32_t)(i * 64 + (__ffsll((long long)bits) - 1));
-            bits &= bits - 1;
-            const int64_t beg = p.in_off[w], deg = p.in_off[w + 1] - beg;
-            // item 0 is w itself, item j >= 1 its (j-1)-th predecessor
-            for (int64_t j0 = 0; j0 <= deg; j0 += 32) {
-                const int64_t j = j0 + lane;
-                const int32_t u = j == 0 ? w : (j <= deg ? __ldg(p.in_src + beg + j - 1) : -1);
-                bool fresh = false;
-                if (u >= 0) {
-                    const unsigned long long bit = 1ull << (u & 63);
-                    fresh = (atomicOr(&p.cand[u >> 6], bit) & bit) == 0ull;
+    // 32 bitmap words per warp iteration (lane l: word i0 + l * nwarps), the
+    // non-zero ones in order
+    for (int64_t i0 = warp; i0 < p.nwords; i0 += nwarps * 32) {
+        const int64_t iw = i0 + (int64_t)lane * nwarps;
+        const unsigned long long mine = iw < p.nwords ? Fc[iw] : 0ull;
+        for (unsigned nz = __ballot_sync(kFull, mine != 0ull); nz; nz &= nz - 1u) {
+            const int src_lane = __ffs(nz) - 1;
+            const int64_t i = i0 + (int64_t)src_lane * nwarps;
+            unsigned long long bits = __shfl_sync(kFull, mine, src_lane);
+            while (bits) {
+                const int32_t w = (int32_t)(i * 64 + (__ffsll((long long)bits) - 1));
+                bits &= bits - 1;
+                const int64_t beg = p.in_off[w], deg = p.in_off[w + 1] - beg;
+                // item 0 is w itself, item j >= 1 its (j-1)-th predecessor
+                for (int64_t j0 = 0; j0 <= deg; j0 += 32) {
+                    const int64_t j = j0 + lane;
+                    const int32_t u = j == 0 ? w : (j <= deg ? __ldg(p.in_src + beg + j - 1) : -1);
+                    bool fresh = false;
+                    if (u >= 0) {
+                        const unsigned long long bit = 1ull << (u & 63);
+                        fresh = (atomicOr(&p.cand[u >> 6], bit) & bit) == 0ull;
+                    }
+                    cand_append(p, fresh, u);
                 }
-                cand_append(p, fresh, u);
             }
         }
     }
@@ -1180,7 +1188,7 @@ constexpr int kScatterRows = (LANES < 2 ? LANES : 2) / VPL > 0 ? (LANES < 2 ? LA
 // Copy the rows of F_t into regs[p^1] (they hold c_{t-1} there) and cut the
 // in-arc lists longer than p.scatter_inline into segments, listed in
 // cand_list[0] (node) / cand_list[1] (segment index), counted in
-// cand_count[0].  A lane per changed node, a warp per bitmap word.
+// cand_count[0].  A lane per changed node, a warp per non-zero bitmap word.
 __global__ void __launch_bounds__(kBlock) k_scatter_seed(Plan p)
 {
     const DevCtl *ctl = p.ctl;
@@ -1195,40 +1203,48 @@ __global__ void __launch_bounds__(kBlock) k_scatter_seed(Plan p)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     uint32_t c_write = 0;
     bool bad = false;
-    for (int64_t i = warp; i < p.nwords; i += nwarps) {
-        const unsigned long long bits = Fc[i];
-        if (bits == 0ull) continue;
+    // a warp reads 32 bitmap words at once (lane l: word i0 + l * nwarps, so
+    // that small bitmaps still spread over all warps), then handles the
+    // non-zero ones in order
+    for (int64_t i0 = warp; i0 < p.nwords; i0 += nwarps * 32) {
+        const int64_t iw = i0 + (int64_t)lane * nwarps;
+        const unsigned long long mine = iw < p.nwords ? Fc[iw] : 0ull;
+        for (unsigned nz = __ballot_sync(kFull, mine != 0ull); nz; nz &= nz - 1u) {
+            const int src_lane = __ffs(nz) - 1;
+            const int64_t i = i0 + (int64_t)src_lane * nwarps;
+            const unsigned long long bits = __shfl_sync(kFull, mine, src_lane);
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h) {
-            const int bit = lane + 32 * h;
-            const int32_t w = (int32_t)(i * 64 + bit);
-            int32_t nseg = 0;
-            if ((bits >> bit) & 1ull) {
+            for (int h = 0; h < 2; ++h) {
+                const int bit = lane + 32 * h;
+                const int32_t w = (int32_t)(i * 64 + bit);
+                int32_t nseg = 0;
+                if ((bits >> bit) & 1ull) {
 #pragma unroll 4
-                for (int k = 0; k < vec; ++k) dst[(int64_t)w * vec + k] = src[(int64_t)w * vec + k];
-                ++c_write;
-                const int64_t d = p.in_off[w + 1] - p.in_off[w];
-                if (d > p.scatter_inline) nseg = (int32_t)((d + p.scatter_seg - 1) / p.scatter_seg);
-            }
-            int32_t incl = nseg;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int32_t t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int32_t total = __shfl_sync(kFull, incl, 31);
-            if (total == 0) continue;
-            unsigned long long base = 0;
-            if (lane == 31) base = atomicAdd(&p.ctl->cand_count[0], (unsigned long long)total);
-            base = __shfl_sync(kFull, base, 31);
-            const unsigned long long first = base + (unsigned long long)(incl - nseg);
-            for (int32_t j = 0; j < nseg; ++j) {
-                if (first + j >= (unsigned long long)p.n) {   // k_prep's bound broken
-                    bad = true;
-                    break;
+                    for (int k = 0; k < vec; ++k) dst[(int64_t)w * vec + k] = src[(int64_t)w * vec + k];
+                    ++c_write;
+                    const int64_t d = p.in_off[w + 1] - p.in_off[w];
+                    if (d > p.scatter_inline) nseg = (int32_t)((d + p.scatter_seg - 1) / p.scatter_seg);
                 }
-                p.cand_list[0][first + j] = w;
-                p.cand_list[1][first + j] = j;
+                int32_t incl = nseg;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int32_t total = __shfl_sync(kFull, incl, 31);
+                if (total == 0) continue;
+                unsigned long long base = 0;
+                if (lane == 31) base = atomicAdd(&p.ctl->cand_count[0], (unsigned long long)total);
+                base = __shfl_sync(kFull, base, 31);
+                const unsigned long long first = base + (unsigned long long)(incl - nseg);
+                for (int32_t j = 0; j < nseg; ++j) {
+                    if (first + j >= (unsigned long long)p.n) {   // k_prep's bound broken
+                        bad = true;
+                        break;
+                    }
+                    p.cand_list[0][first + j] = w;
+                    p.cand_list[1][first + j] = j;
+                }
             }
         }
     }
@@ -1367,25 +1383,32 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_scatter(Plan p)
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nseg = min((int64_t)ctl->cand_count[0], p.n);   // the list's capacity
-    const int64_t total = nseg + p.nwords;
     uint32_t pairs = 0, raised = 0;
     MarkTally mt;
     bool bad = false;
-    for (int64_t it = warp; it < total; it += nwarps) {
-        if (it < nseg) {
-            int32_t w = -1, cnt = 0;
-            int64_t beg = 0;
-            if (lane == 0) {
-                w = p.cand_list[0][it];
-                const int64_t j = p.cand_list[1][it];
-                const int64_t b0 = p.in_off[w], d = p.in_off[w + 1] - b0;
-                beg = b0 + j * p.scatter_seg;
-                cnt = (int32_t)min((int64_t)p.scatter_seg, d - j * p.scatter_seg);
-            }
-            scatter_entries<LANES, VPL>(p, cur, w, beg, cnt, mt, pairs, raised, bad);
-        } else {
-            const int64_t i = it - nseg;
-            const unsigned long long bits = Fc[i];
+    for (int64_t it = warp; it < nseg; it += nwarps) {
+        int32_t w = -1, cnt = 0;
+        int64_t beg = 0;
+        if (lane == 0) {
+            w = p.cand_list[0][it];
+            const int64_t j = p.cand_list[1][it];
+            const int64_t b0 = p.in_off[w], d = p.in_off[w + 1] - b0;
+            beg = b0 + j * p.scatter_seg;
+            cnt = (int32_t)min((int64_t)p.scatter_seg, d - j * p.scatter_seg);
+        }
+        scatter_entries<LANES, VPL>(p, cur, w, beg, cnt, mt, pairs, raised, bad);
+    }
+    // the bitmap words of F_t, 32 per warp iteration (lane l: word i0 + l *
+    // nwarps; the warps that finished their segments first take the first
+    // ones)
+    const int64_t wrank = (warp - nseg % nwarps + nwarps) % nwarps;
+    for (int64_t i0 = wrank; i0 < p.nwords; i0 += nwarps * 32) {
+        const int64_t iw = i0 + (int64_t)lane * nwarps;
+        const unsigned long long mine = iw < p.nwords ? Fc[iw] : 0ull;
+        for (unsigned nz = __ballot_sync(kFull, mine != 0ull); nz; nz &= nz - 1u) {
+            const int src_lane = __ffs(nz) - 1;
+            const int64_t i = i0 + (int64_t)src_lane * nwarps;
+            const unsigned long long bits = __shfl_sync(kFull, mine, src_lane);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 if (((bits >> (32 * h)) & 0xffffffffull) == 0ull) continue;
@@ -1658,18 +1681,25 @@ __global__ void __launch_bounds__(kBlock) k_est_changed(Plan p)
         }
         cnt -= k;
     };
-    for (int64_t w = warp; w < p.nwords; w += nwarps) {
-        const unsigned long long bits = Fc[w];
-        if (bits == 0ull) continue;
+    // 32 bitmap words per warp iteration (lane l: word i0 + l * nwarps), the
+    // non-zero ones in order
+    for (int64_t w0 = warp; w0 < p.nwords; w0 += nwarps * 32) {
+        const int64_t ww = w0 + (int64_t)lane * nwarps;
+        const unsigned long long mine = ww < p.nwords ? Fc[ww] : 0ull;
+        for (unsigned nz = __ballot_sync(kFull, mine != 0ull); nz; nz &= nz - 1u) {
+            const int src_lane = __ffs(nz) - 1;
+            const int64_t w = w0 + (int64_t)src_lane * nwarps;
+            const unsigned long long bits = __shfl_sync(kFull, mine, src_lane);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const bool b = (bits >> (32 * h + lane)) & 1ull;
-            const unsigned bal = __ballot_sync(kFull, b);
-            if (b) q[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)(w * 64 + 32 * h + lane);
-            cnt += __popc(bal);
+            for (int h = 0; h < 2; ++h) {
+                const bool b = (bits >> (32 * h + lane)) & 1ull;
+                const unsigned bal = __ballot_sync(kFull, b);
+                if (b) q[cnt + __popc(bal & ((1u << lane) - 1u))] = (int32_t)(w * 64 + 32 * h + lane);
+                cnt += __popc(bal);
+            }
+            __syncwarp();
+            while (cnt >= 32) drain(32);
         }
-        __syncwarp();
-        while (cnt >= 32) drain(32);
     }
     if (cnt > 0) drain(cnt);
     __syncwarp();
@@ -1702,10 +1732,14 @@ __global__ void __launch_bounds__(kBlock) k_init(Plan p)
 {
     const int64_t cpr = p.W >> 4;
     const int64_t total = p.n * cpr;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = c / cpr;
-        const int byte0 = (int)(c - v * cpr) << 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // chunk c = v * cpr + j, advanced by the grid stride without a division
+    // per chunk
+    const int64_t c0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t dv = stride / cpr, dj = stride - dv * cpr;
+    int64_t v = c0 / cpr, j = c0 - v * cpr;
+    for (int64_t c = c0; c < total; c += stride) {
+        const int byte0 = (int)j << 4;
         const int r = byte0 >> p.b;
         const int o = byte0 & (p.m - 1);
         uint64_t item = p.orig_id ? (uint64_t)__ldg(p.orig_id + v) : (uint64_t)v;
@@ -1726,6 +1760,12 @@ __global__ void __launch_bounds__(kBlock) k_init(Plan p)
         const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
         reinterpret_cast<uint4 *>(p.regs[0])[c] = val;
         if (__ldg(p.off + v + 1) == __ldg(p.off + v)) reinterpret_cast<uint4 *>(p.regs[1])[c] = val;
+        v += dv;
+        j += dj;
+        if (j >= cpr) {
+            j -= cpr;
+            ++v;
+        }
     }
 }
 
