@@ -87,7 +87,7 @@ struct Layout {
     size_t blk_q, est_acc, ecache, hist, lc, seeds, ctl, scan_tmp, blk_counts, blk_offs;
     size_t seg_counts, seg_offs, totals, perm, inv, off2, tgt2, rcounts, roffs, stage;
     size_t ns_prev, ns_dist, ns_reach, ns_ecc, ns_rad;
-    size_t slot_T, slot_changed, blk_graph, g_base, g_nodes;
+    size_t slot_T, slot_changed, blk_graph, g_base, g_nodes, hr;
     size_t total;
 };
 
@@ -192,6 +192,7 @@ Layout make_layout(const Sizes &s)
     L.blk_q = take(16 * s.nwords * s.R);
     L.est_acc = take(16 * (size_t)s.S);
     L.ecache = s.est_fused ? take(8 * rows * (size_t)s.R) : 0;
+    L.hr = s.layout == 0 ? take(2 * rows * (size_t)s.R) : 0;
     L.hist = take(8 * (size_t)s.history * s.S);
     L.lc = take(8 * (s.m + 1));
     L.seeds = take(8 * (size_t)s.S);
@@ -569,6 +570,7 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.est_acc = reinterpret_cast<unsigned long long *>(ws + L.est_acc);
     p.est_fused = s.est_fused ? 1 : 0;
     p.ecache = s.est_fused ? reinterpret_cast<double *>(ws + L.ecache) : nullptr;
+    p.hr = s.layout == 0 ? reinterpret_cast<uint16_t *>(ws + L.hr) : nullptr;
     p.hist = reinterpret_cast<double *>(ws + L.hist);
     p.lc = reinterpret_cast<const double *>(ws + L.lc);
     p.seeds = reinterpret_cast<const uint64_t *>(ws + L.seeds);
@@ -714,6 +716,8 @@ int hanf_create(hanf_ctx **out, int64_t n, int64_t arcs, const int64_t *offsets,
     p.warp_variant = ((o.gather_variant == 2 || o.gather_variant == 4) && p.union_async_warps > 0) ? 2 : 1;
     // asynchronous copies in the small-degree kernel by default (rows of at
     // most 128 bytes; measured 26.4 -> 25.1 ms a dense R-MAT 27 pass)
+    // pass 0 from the two-byte c_0 records (byte layout, rows up to 1 KB)
+    p.first_warps = p.hr ? hanf::first_pass_warps(s.W, c->nsm) : 0;
     p.small_variant = ((o.gather_variant == 0 || o.gather_variant >= 3) && !s.layout &&
                        s.W <= 128 && hanf::small_async_blocks(s.W) > 0)
                           ? 3

@@ -85,6 +85,8 @@ struct Plan {
     int32_t *slot_T;                  // S: first pass that left the slot unchanged
     unsigned long long *slot_changed; // S: nodes changed in the slot this pass
     const int32_t *orig_id;           // input id of every stored node (null: identity)
+    uint16_t *hr;                     // c_0 as (index << 8) | rho+ of node v, run r at
+                                      // [v * R + r] (byte layout; null otherwise)
     // per-node statistics of the E_v(t) sequence, [run][node] (node_stats)
     double *ns_prev;                  // E_v at the last estimate
     double *ns_dist;                  // sum_t t (E_v(t) - E_v(t-1))
@@ -102,6 +104,8 @@ struct Plan {
     int32_t union_async_warps;        // resident warps of the asynchronous-copy variant
     int32_t warp_variant;             // medium/hub gathers: 1 register batches, 2 async copies
     int32_t small_variant;            // small-degree dense gathers: 0 registers, 3 async copies
+    int32_t first_warps;              // pass 0 from the c_0 records: resident warps of its
+                                      // kernels (0 = pass 0 reads rows like the others)
     DevCtl *ctl;
 };
 
@@ -135,6 +139,7 @@ cudaError_t launch_shard_apply(const Plan &p, const int32_t *perm, const int32_t
                                const uint8_t *rows, int64_t k, cudaStream_t s);
 int union_occupancy_warps(int W, int nsm);
 int small_async_blocks(int W);
+int first_pass_warps(int W, int nsm);   // resident warps of the pass-0 kernels (0: none)
 int scatter_occupancy_warps(int W, int nsm);
 int packed_occupancy_warps(int m, int nsm);
 int union_async_warps(int W, int nsm);

@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_small(Plan p)
     constexpr int GPW = 32 / LANES;
     constexpr int U = 4 / VPL > 0 ? 4 / VPL : 1;
     const DevCtl *ctl = p.ctl;
-    if (ctl->done || ctl->mode == kModeScatter) return;
+    if (ctl->done || ctl->mode == kModeScatter || (ctl->t == 0 && p.first_warps)) return;
     if constexpr (has_sparse_path<LANES, VPL>()) {
         if (SPARSE != (ctl->mode != kModeDense)) return;
     }
@@ -648,7 +648,7 @@ template <int LANES, int VPL>
 __global__ void __launch_bounds__(kBlock, min_blocks(VPL)) k_union_warp(Plan p)
 {
     const DevCtl *ctl = p.ctl;
-    if (ctl->done || ctl->mode == kModeScatter) return;
+    if (ctl->done || ctl->mode == kModeScatter || (ctl->t == 0 && p.first_warps)) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
     const bool test = ctl->mode != kModeDense;
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_union_warp_async(Plan p)
     static_assert(GPW * LANES == 32, "lane groups tile the warp");
     extern __shared__ uint4 smem_raw[];
     const DevCtl *ctl = p.ctl;
-    if (ctl->done || ctl->mode == kModeScatter) return;
+    if (ctl->done || ctl->mode == kModeScatter || (ctl->t == 0 && p.first_warps)) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
     const bool test = ctl->mode != kModeDense;
@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_union_small_async(Plan p)
     constexpr int TPL = (UA + LANES - 1) / LANES;
     extern __shared__ uint4 async_rows[];
     const DevCtl *ctl = p.ctl;
-    if (ctl->done || ctl->mode != kModeDense) return;
+    if (ctl->done || ctl->mode != kModeDense || (ctl->t == 0 && p.first_warps)) return;
     const int cur = ctl->parity;
     const bool first = ctl->t == 0;
     const uint8_t *rc = p.regs[cur];
@@ -1025,6 +1025,163 @@ __global__ void __launch_bounds__(kBlock) k_hub_finish(Plan p)
         warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
     }
     flush_counters(p, cur, mt, 0u, 0u, c_own, c_write);
+}
+
+// ---------------------------------------------------------------- pass 0 from the c_0 records
+
+// At t = 0 every counter holds its own node only: run r's register idx_r(u)
+// = rho_r(u), every other register 0 (Algorithm 2's initialisation).  So
+// pass 0, c_1[v] = max(c_0[v], max_{v->w} c_0[w]), needs one two-byte record
+// (idx << 8 | rho) a successor and run, written by k_init, instead of the
+// successor's W-byte row: one sector request instead of W/32.  The successors'
+// registers are merged into a row of one 32-bit word a register in shared
+// memory (atomicMax), which is then packed into bytes and finished as in the
+// other passes.  The result is the same row, so the pass is the same; the
+// pull kernels sit it out (they return at t = 0 when first_warps is set).
+
+// Lane gl's 16-byte chunk of a shared-memory row of word registers, cleared
+// behind it for the next node.
+__device__ __forceinline__ uint4 pack_chunk(uint32_t *row_words, int byte0)
+{
+    uint4 *q = reinterpret_cast<uint4 *>(row_words + byte0);
+    uint32_t out[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint4 a = q[i];
+        out[i] = a.x | (a.y << 8) | (a.z << 16) | (a.w << 24);
+        q[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+// Merge the records of arcs [e0, end) taken `stride` apart, KB at a time, into
+// the word row: every run's register of every successor.
+template <int KB>
+__device__ __forceinline__ void merge_records(const Plan &p, uint32_t *row_words, int64_t e0,
+                                              int64_t end, int stride)
+{
+    for (; e0 < end; e0 += (int64_t)KB * stride) {
+        int32_t w[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            const int64_t e = e0 + (int64_t)k * stride;
+            w[k] = e < end ? __ldg(p.tgt + e) : -1;
+        }
+        for (int r = 0; r < p.R; ++r) {
+            uint32_t rec[KB];
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                rec[k] = w[k] >= 0 ? (uint32_t)__ldg(p.hr + (int64_t)w[k] * p.R + r) : 0u;
+#pragma unroll
+            for (int k = 0; k < KB; ++k)
+                if (w[k] >= 0) atomicMax(row_words + r * p.m + (rec[k] >> 8), rec[k] & 0xffu);
+        }
+    }
+}
+
+// The node's own counter c_0[v], lane gl's chunks.
+template <int LANES, int VPL>
+__device__ __forceinline__ void own_singleton(Row<LANES, VPL> &own, const Plan &p, int32_t v, int gl)
+{
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) {
+        const int byte0 = (k * LANES + gl) << 4;
+        const uint32_t e = __ldg(p.hr + (int64_t)v * p.R + (byte0 >> p.b));
+        const int rel = (int)(e >> 8) - (byte0 & (p.m - 1));
+        const uint32_t val = (rel >= 0 && rel < 16) ? (e & 0xffu) << ((rel & 3) * 8) : 0u;
+        const int q = rel >> 2;
+        own.v[k] = make_uint4(q == 0 ? val : 0u, q == 1 ? val : 0u, q == 2 ? val : 0u,
+                              q == 3 ? val : 0u);
+    }
+}
+
+constexpr int kFirstBlocks = 4;   // resident blocks an SM the pass-0 kernels are built for
+
+// Pass 0 over small nodes: a lane group per node, as k_union_small.
+template <int LANES, int VPL>
+__global__ void __launch_bounds__(kBlock, kFirstBlocks) k_first_small(Plan p)
+{
+    constexpr int GPW = 32 / LANES;
+    constexpr int WB = 16 * LANES * VPL;   // registers a row (all runs)
+    __shared__ __align__(16) uint32_t words[kBlock / 32][GPW * WB];
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done || ctl->t != 0 || p.first_warps == 0) return;
+    const int cur = ctl->parity;
+    const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
+    uint32_t *row_words = words[threadIdx.x >> 5] + g * WB;
+    for (int i = gl; i < WB; i += LANES) row_words[i] = 0u;
+    __syncwarp();
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_scan = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
+    const int64_t count = p.n_small;
+    const int64_t stride = nwarps * GPW;
+    int64_t idx = warp * GPW + g;
+    int32_t v_next = idx < count ? __ldg(p.nodes + idx) : -1;
+    for (int64_t base = warp * GPW; base < count; base += stride) {
+        const int32_t v = v_next;
+        idx += stride;
+        v_next = idx < count ? __ldg(p.nodes + idx) : -1;
+        const bool valid = v >= 0;
+        const int64_t beg = valid ? __ldg(p.off + v) : 0, end = valid ? __ldg(p.off + v + 1) : 0;
+        merge_records<8>(p, row_words, beg + gl, end, LANES);
+        __syncwarp();
+        Row<LANES, VPL> acc, own;
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) acc.v[k] = pack_chunk(row_words, (k * LANES + gl) << 4);
+        if (valid) own_singleton(own, p, v, gl);
+        __syncwarp();
+        if (valid && gl == 0) c_scan += (uint32_t)(end - beg);
+        // every listed node has arcs; pass 0 stores every row it visits
+        const uint32_t mask = node_finish(p, cur, acc, valid, true, v, gl, c_own, c_write, &own);
+        warp_mark(p, cur, gl == 0 && valid, v, mask, mt);
+    }
+    flush_counters(p, cur, mt, c_scan, gl == 0 ? c_scan : 0u, c_own, c_write);
+}
+
+// Pass 0 over hub segments and medium nodes: a warp per item, as k_union_warp.
+template <int LANES, int VPL>
+__global__ void __launch_bounds__(kBlock, kFirstBlocks) k_first_warp(Plan p)
+{
+    constexpr int WB = 16 * LANES * VPL;
+    __shared__ __align__(16) uint32_t words[kBlock / 32][WB];
+    const DevCtl *ctl = p.ctl;
+    if (ctl->done || ctl->t != 0 || p.first_warps == 0) return;
+    const int cur = ctl->parity;
+    const int lane = threadIdx.x & 31, g = lane / LANES, gl = lane % LANES;
+    uint32_t *row_words = words[threadIdx.x >> 5];
+    for (int i = lane; i < WB; i += 32) row_words[i] = 0u;
+    __syncwarp();
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t c_scan = 0, c_own = 0, c_write = 0;
+    MarkTally mt;
+    const int64_t total = p.n_seg + p.n_med;
+    for (int64_t it = warp; it < total; it += nwarps) {
+        const bool seg = it < p.n_seg;
+        const int32_t v = seg ? __ldg(p.seg_node + it) : __ldg(p.nodes + p.n_small + (it - p.n_seg));
+        const int64_t beg = seg ? __ldg(p.seg_beg + it) : __ldg(p.off + v);
+        const int64_t end = seg ? __ldg(p.seg_end + it) : __ldg(p.off + v + 1);
+        merge_records<4>(p, row_words, beg + lane, end, 32);
+        __syncwarp();
+        Row<LANES, VPL> acc, own;
+        if (g == 0) {
+#pragma unroll
+            for (int k = 0; k < VPL; ++k) acc.v[k] = pack_chunk(row_words, (k * LANES + gl) << 4);
+        }
+        __syncwarp();
+        if (lane == 0) c_scan += (uint32_t)(end - beg);
+        if (seg) {
+            if (g == 0) row_store(p.hub_part, it, acc, gl);
+            if (lane == 0) p.hub_any[it] = end > beg ? 1 : 0;
+        } else {
+            if (g == 0) own_singleton(own, p, v, gl);
+            const uint32_t mask = node_finish(p, cur, acc, g == 0, true, v, gl, c_own, c_write, &own);
+            warp_mark(p, cur, lane == 0, v, mask, mt);
+        }
+    }
+    flush_counters(p, cur, mt, c_scan, lane == 0 ? c_scan : 0u, c_own, c_write);
 }
 
 // ---------------------------------------------------------------- pass control
@@ -1756,7 +1913,11 @@ __global__ void __launch_bounds__(kBlock) k_init(Plan p)
         rho = rho > 31 ? 31 : rho;
         uint32_t w[4] = {0u, 0u, 0u, 0u};
         const int rel = idx - o;
-        if (rel >= 0 && rel < 16) w[rel >> 2] = (uint32_t)rho << ((rel & 3) * 8);
+        if (rel >= 0 && rel < 16) {
+            w[rel >> 2] = (uint32_t)rho << ((rel & 3) * 8);
+            // the chunk holding the register also records it for pass 0
+            if (p.hr) p.hr[v * p.R + r] = (uint16_t)((idx << 8) | rho);
+        }
         const uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
         reinterpret_cast<uint4 *>(p.regs[0])[c] = val;
         if (__ldg(p.off + v + 1) == __ldg(p.off + v)) reinterpret_cast<uint4 *>(p.regs[1])[c] = val;
@@ -2726,6 +2887,15 @@ struct UnionKernels {
             cudaStreamWaitEvent(fk->side, fk->fork, 0);
             ss = fk->side;
         }
+        if constexpr (VPL <= 2) {
+            if (p.first_warps > 0) {   // pass 0 from the c_0 records (other passes: returns)
+                const int64_t fpersistent = (p.first_warps * 32 + kBlock - 1) / kBlock;
+                const int fw = (int)std::max<int64_t>(1, std::min(fpersistent, (warp_items + WPB - 1) / WPB));
+                const int fs = (int)std::max<int64_t>(1, std::min(fpersistent, (small_items + WPB - 1) / WPB));
+                k_first_warp<LANES, VPL><<<fw, kBlock, 0, s>>>(p);
+                k_first_small<LANES, VPL><<<fs, kBlock, 0, ss>>>(p);
+            }
+        }
         if constexpr (VPL == 1 && LANES <= 8) {
             if (p.warp_variant == 2) {
                 using Cfg = AsyncCfg<LANES>;
@@ -2791,6 +2961,18 @@ struct UnionKernels {
             return 0;
         }
     }
+    // Resident blocks of the pass-0 kernels (0 where they do not apply).
+    static int first_occupancy()
+    {
+        if constexpr (VPL <= 2) {
+            int a = 0, b = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_first_small<LANES, VPL>, kBlock, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_first_warp<LANES, VPL>, kBlock, 0);
+            return a < b ? a : b;
+        } else {
+            return 0;
+        }
+    }
     // Resident blocks of the asynchronous-copy warp kernel (0 where it does
     // not apply); also opts it in to more than 48 KB of shared memory.
     static int async_occupancy()
@@ -2838,6 +3020,16 @@ int small_async_blocks(int W)
         return cudaSuccess;
     });
     return nb;
+}
+
+int first_pass_warps(int W, int nsm)
+{
+    int nb = 0;
+    with_width(W, [&](auto k) {
+        nb = decltype(k)::first_occupancy();
+        return cudaSuccess;
+    });
+    return nb * nsm * (kBlock / 32);
 }
 
 int union_async_warps(int W, int nsm)

@@ -62,9 +62,10 @@ def test_results_same_alone_and_in_the_mix(H, oracle):
 
 
 def test_admission_by_footprint(H):
-    """An arena that fits one job at a time still serves them all in order."""
+    """An arena that fits one job at a time still serves them all in order.
+    The graphs have more than 65,536 nodes, so no two jobs share a context."""
     from paper_1011_5599_gb300.hanf import make_opts, workspace_size
-    off, tgt = G.rmat(12, seed=1)
+    off, tgt = G.rmat(17, seed=1)
     need = workspace_size(off.size - 1, tgt.size, 6, make_opts()[0], True)
     with H.Server(need + (1 << 20), workers=4) as srv:
         ids = [srv.submit(off, tgt, 6, SEED + k) for k in range(6)]
