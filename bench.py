@@ -173,13 +173,17 @@ def ncu_traffic(workload, layout="byte"):
     return float(rec["traffic_bytes_per_launch"])
 
 
-def union_bytes(row, n, row_bytes):
+def union_bytes(row, n, row_bytes, record_bytes=0):
     """Algorithmic bytes of one pass's union launches from its trace row: 4
     per scanned arc (target id), a row per gathered successor, own counter
     read and counter written, the offsets of every node in a pull pass over
-    all nodes (8 n), and the changed-node bitmaps read and written (n / 4)."""
-    b = 4 * row["arcs_scanned"] + row_bytes * (row["arcs_gathered"] + row["own_reads"]
-                                               + row["writes"])
+    all nodes (8 n), and the changed-node bitmaps read and written (n / 4).
+    Pass 0 reads a c_0 record of record_bytes (2 per run) per successor and
+    own counter instead of a row where the library has them (byte layout,
+    rows up to 1 KB; record_bytes = 0: rows)."""
+    got = record_bytes if (record_bytes and int(row["t"]) == 0) else row_bytes
+    b = 4 * row["arcs_scanned"] + got * (row["arcs_gathered"] + row["own_reads"]) + \
+        row_bytes * row["writes"]
     if int(row["mode"]) in (0, 2):
         b += 8 * n
     return b + n / 4
@@ -586,6 +590,7 @@ def main():
     m = 1 << log2m
     W = m * R
     row_bytes = 5 * m // 8 if args.layout == "packed" else W   # bytes per stored counter row
+    rec_bytes = 2 * R if args.layout == "byte" and W <= 1024 else 0   # pass 0's c_0 records
     t_gen = time.perf_counter()
     off, tgt = make_graph(wl, args.seed + rank, device)
     torch.cuda.synchronize()
@@ -646,19 +651,21 @@ def main():
         hp.run()
         rows = hp.trace()
         prof_ms += sum(r["union_ms"] for r in rows)
-        prof_bytes += sum(union_bytes(r, n, row_bytes) for r in rows)
+        prof_bytes += sum(union_bytes(r, n, row_bytes, rec_bytes) for r in rows)
         prof_gathered += hp.counters()["arcs_gathered"] * m * R
         for r in rows:
-            if int(r["mode"]) == 2:          # dense pull passes: the dominant launches
+            # dense pull passes that gather rows (pass 0 reads c_0 records
+            # where they exist): the dominant launches
+            if int(r["mode"]) == 2 and (int(r["t"]) > 0 or not rec_bytes):
                 dense_ms += r["union_ms"]
-                dense_bytes += union_bytes(r, n, row_bytes)
+                dense_bytes += union_bytes(r, n, row_bytes, rec_bytes)
                 dense_n += 1
     psteps = max(args.profile_steps, 1)
     if prof_gathered != psteps * gathered / args.steps:
         raise RuntimeError("the profiled run gathered a different number of counters")
     if args.trace:
         for row in rows:
-            gbs = union_bytes(row, n, row_bytes) / (row["union_ms"] * 1e6)
+            gbs = union_bytes(row, n, row_bytes, rec_bytes) / (row["union_ms"] * 1e6)
             print(json.dumps({**row, "algorithmic_GBps": gbs}), file=sys.stderr)
     union_s = prof_ms / 1e3 / psteps                  # union-kernel seconds per step
     union_launch_ms = prof_ms / max(len(rows) * psteps, 1)
@@ -720,7 +727,8 @@ def main():
     all_gbs = bytes_per_launch / (union_launch_ms / 1e3) / 1e9 if union_launch_ms > 0 else None
     if dense_n:
         launch_bytes, launch_ms = dense_bytes / dense_n, dense_ms / dense_n
-        kernel = "union launches of a dense pull pass (k_union_small_async, k_union_warp, ...)"
+        kernel = ("union launches of a dense pull pass that gathers rows, t >= 1 "
+                  "(k_union_small_async, k_union_warp, ...)")
     else:
         launch_bytes, launch_ms = bytes_per_launch, union_launch_ms
         kernel = "union launches of one pass (k_union_*, k_scatter*, k_hub_finish)"
