@@ -419,7 +419,8 @@ int pass_launch_count(const hanf_ctx *c)
     const Plan &p = c->plan;
     const bool scatter = !p.layout && p.in_off && p.scatter_den > 0;
     return 5 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (p.S > 8 ? 1 : 0) +
-           (!p.layout && p.W <= 128 ? 1 : 0) + (scatter ? 2 : 0) + (p.est_fused ? 3 : 2);
+           (!p.layout && p.W <= 128 ? 1 : 0) + (scatter ? 2 : 0) + (p.est_fused ? 3 : 2) +
+           (!p.layout && p.first_warps > 0 ? 2 : 0);   // the pass-0 kernels
 }
 
 }  // namespace

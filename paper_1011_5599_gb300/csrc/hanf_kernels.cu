@@ -1067,6 +1067,30 @@ __device__ __forceinline__ void merge_records(const Plan &p, uint32_t *row_words
             const int64_t e = e0 + (int64_t)k * stride;
             w[k] = e < end ? __ldg(p.tgt + e) : -1;
         }
+        if (p.R == 8) {
+            // eight runs: a successor's records are one aligned 16-byte vector
+            // (four successors at a time)
+#pragma unroll
+            for (int k0 = 0; k0 < KB; k0 += 4) {
+                uint4 rec[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    rec[k] = (k0 + k < KB && w[k0 + k] >= 0)
+                                 ? __ldg(reinterpret_cast<const uint4 *>(p.hr) + w[k0 + k])
+                                 : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k0 + k < KB && w[k0 + k] >= 0) {
+                        const uint32_t q[4] = {rec[k].x, rec[k].y, rec[k].z, rec[k].w};
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const uint32_t e = (q[r >> 1] >> (16 * (r & 1))) & 0xffffu;
+                            atomicMax(row_words + r * p.m + (e >> 8), e & 0xffu);
+                        }
+                    }
+            }
+            continue;
+        }
         for (int r = 0; r < p.R; ++r) {
             uint32_t rec[KB];
 #pragma unroll
@@ -3180,7 +3204,8 @@ cudaError_t launch_pass_union(const Plan &p, cudaStream_t s, cudaEvent_t ev0, cu
     if (ev1) cudaEventRecord(ev1, s);
     if (nlaunch)
         *nlaunch += 3 + (p.in_off ? 1 : 0) + (p.n_hub ? 1 : 0) + (!p.layout && p.W <= 128 ? 1 : 0) +
-                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0);
+                    (!p.layout && p.in_off && p.scatter_den > 0 ? 2 : 0) +
+                    (!p.layout && p.first_warps > 0 ? 2 : 0);
     return cudaGetLastError();
 }
 
