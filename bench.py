@@ -701,9 +701,13 @@ def main():
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        create_s = 0.0   # of which context creation (upload, validation, relabelling, transpose)
         for _ in range(args.e2e_steps):
+            tc = time.perf_counter()
             with HyperANF(off_h, tgt_h, log2m, 0x5EED, runs=R, frontier="auto",
                           device=device, use_graph=args.driver == "graph") as he:
+                torch.cuda.synchronize()
+                create_s += time.perf_counter() - tc
                 Ne, Te = he.run()
                 e_merges += he.counters()["arcs_gathered"] * m * R
                 d2h += sum(x.nbytes for x in Ne)
@@ -713,7 +717,8 @@ def main():
         e2e = {"value": e_merges / e_el, "unit": UNIT,
                "h2d_bytes_per_step": int((n + 1) * 8 + arcs * 4),
                "d2h_bytes_per_step": int(d2h // args.e2e_steps),
-               "ms_per_step": 1e3 * e_el / args.e2e_steps}
+               "ms_per_step": 1e3 * e_el / args.e2e_steps,
+               "create_ms_per_step": 1e3 * create_s / args.e2e_steps}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
