@@ -97,7 +97,7 @@ def test_rmat_hubs(H, oracle):
     check_run(H, oracle, off, tgt, 7, frontier="pull", hub_min_deg=64)
 
 
-@pytest.mark.parametrize("R,log2m", [(2, 4), (4, 6), (8, 6), (8, 8), (2, 8)])
+@pytest.mark.parametrize("R,log2m", [(2, 4), (4, 6), (8, 6), (8, 8), (2, 8), (8, 4), (4, 8)])
 def test_batched_runs(H, oracle, R, log2m):
     off, tgt = G.web(1 << 12, seed=7)
     check_run(H, oracle, off, tgt, log2m, R=R)
