@@ -189,6 +189,20 @@ def union_bytes(row, n, row_bytes, record_bytes=0):
     return b + n / 4
 
 
+def dense_row_passes(rows, n, row_bytes, record_bytes=0):
+    """(time ms, algorithmic bytes, count) of the dense pull passes that
+    gather rows: the roofline's dominant launches.  Pass 0 reads c_0 records
+    instead of rows where the library has them (record_bytes > 0) and is left
+    out."""
+    ms, nbytes, count = 0.0, 0.0, 0
+    for r in rows:
+        if int(r["mode"]) == 2 and (int(r["t"]) > 0 or not record_bytes):
+            ms += r["union_ms"]
+            nbytes += union_bytes(r, n, row_bytes, record_bytes)
+            count += 1
+    return ms, nbytes, count
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -653,13 +667,10 @@ def main():
         prof_ms += sum(r["union_ms"] for r in rows)
         prof_bytes += sum(union_bytes(r, n, row_bytes, rec_bytes) for r in rows)
         prof_gathered += hp.counters()["arcs_gathered"] * m * R
-        for r in rows:
-            # dense pull passes that gather rows (pass 0 reads c_0 records
-            # where they exist): the dominant launches
-            if int(r["mode"]) == 2 and (int(r["t"]) > 0 or not rec_bytes):
-                dense_ms += r["union_ms"]
-                dense_bytes += union_bytes(r, n, row_bytes, rec_bytes)
-                dense_n += 1
+        d_ms, d_bytes, d_n = dense_row_passes(rows, n, row_bytes, rec_bytes)
+        dense_ms += d_ms
+        dense_bytes += d_bytes
+        dense_n += d_n
     psteps = max(args.profile_steps, 1)
     if prof_gathered != psteps * gathered / args.steps:
         raise RuntimeError("the profiled run gathered a different number of counters")
